@@ -1,0 +1,350 @@
+"""Benchmark: achieved HBM GB/s per gate on a 30-qubit complex128 state.
+
+Workload (one step): a 30-qubit complex128 state (16 GiB) of normalised
+i.i.d. complex Gaussian amplitudes; one Haar-random 2x2 gate on each target
+0..29, then Haar-random 4x4 gates on 64 random distinct (t0, t1) pairs.  The
+metric is algorithmic bytes (read + write of every amplitude a gate touches,
+2 * 16 * 2^30 per gate) over the step's device time.
+
+Prints one JSON line.  --impl reference times the CPU oracle on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "HBM GB/s per gate (30q c128) vs peak; served circuits/s + p99, c64 vs c128"
+UNIT = "GB/s"
+N_QUBITS = 30
+N_PAIRS = 64
+SEED_STATE = 2507
+SEED_GATES = 2507
+WORKLOAD = "gate sweep, 30-qubit complex128 state (16 GiB): Haar 1q on targets 0..29 + Haar 2q on 64 random pairs"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
+    ap.add_argument("--math", default="df", choices=["df", "fp64"])
+    ap.add_argument("--n", type=int, default=N_QUBITS)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Workload
+# ---------------------------------------------------------------------------
+def make_gates(n):
+    g1s, g2s = W.gate_sweep(n, N_PAIRS, seed=SEED_GATES)
+    return g1s + g2s
+
+
+def gate_bytes(n, amp_bytes):
+    return 2 * amp_bytes * (1 << n)
+
+
+def kernel_kind(g):
+    return "k_dense1" if g.kind == "u1" else "k_dense2"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def time_oracle_sample(psi, gates, budget_s):
+    """Apply gates one by one with the oracle until budget_s has passed;
+    return (GB/s over the gates done, gates done, seconds)."""
+    import oracle as O
+
+    O.build()
+    n = int(psi.size).bit_length() - 1
+    done, t_total, moved = 0, 0.0, 0
+    for g in gates:
+        t0 = time.perf_counter()
+        O.apply_gate(psi, g)
+        t_total += time.perf_counter() - t0
+        moved += gate_bytes(n, 16)
+        done += 1
+        if t_total >= budget_s:
+            break
+    return moved / t_total / 1e9, done, t_total
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = args.n
+    gates = make_gates(n)
+    psi = W.random_state(n, SEED_STATE)
+    # Each step: the next two gates of the sweep (one 1q, one 2q) on the full
+    # state, bounded to about 15 s of single-thread CPU work.
+    order = [gates[i % n] if j % 2 == 0 else gates[n + (i % N_PAIRS)] for i in range(64) for j in range(2)]
+    cursor = 0
+
+    def step():
+        nonlocal cursor
+        gbs, done, secs = time_oracle_sample(psi, order[cursor:cursor + 2], budget_s=1e9)
+        cursor += done
+        return gbs, secs, done
+
+    for _ in range(args.warmup):
+        step()
+    vals, secs_all, gates_done = [], 0.0, 0
+    for _ in range(args.steps):
+        gbs, secs, done = step()
+        vals.append(gbs)
+        secs_all += secs
+        gates_done += done
+    value = gates_done * gate_bytes(n, 16) / secs_all / 1e9
+    sample = f"{gates_done} gates (alternating 1q and 2q from the sweep) on the full {n}-qubit state"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs_all / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_qubits": n, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    from paper_2506_09198_gb300 import build
+
+    build.build()
+    from paper_2506_09198_gb300 import qs
+
+    n = args.n
+    c64 = args.dtype == "c64"
+    amp_bytes = 8 if c64 else 16
+    dt = qs.QS_C64 if c64 else qs.QS_C128
+    math_mode = qs.QS_MATH_FP64 if args.math == "fp64" else qs.QS_MATH_DF
+    gates = make_gates(n)
+    psi_host = W.random_state(n, SEED_STATE + rank)
+    if c64:
+        psi_host = psi_host.astype(np.complex64)
+    # pinned host copy for the end-to-end measurement
+    pinned = torch.empty(psi_host.nbytes, dtype=torch.uint8, pin_memory=True)
+    pinned.numpy()[:] = psi_host.view(np.uint8)
+
+    stream = torch.cuda.Stream()
+    st = qs.State(n, dt, math_mode)
+    qs.qs_set_stream(st.h, stream.cuda_stream)
+    host_in = pinned.numpy()
+    qs.qs_copy_in(st.h, host_in)
+    st.sync()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    def one_step(events=None):
+        for i, g in enumerate(gates):
+            if events is not None:
+                events[i][0].record(stream)
+            st.apply(g)
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    barrier()
+
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in gates]
+          for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for s in range(args.steps):
+        one_step(ev[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    bytes_step = len(gates) * gate_bytes(n, amp_bytes)
+    value = world * bytes_step * args.steps / (ms * 1e-3) / 1e9
+
+    # Per-kernel averages over the timed region.
+    per_kind = {}
+    for s in range(args.steps):
+        for i, g in enumerate(gates):
+            d = ev[s][i][0].elapsed_time(ev[s][i][1])
+            per_kind.setdefault(kernel_kind(g), []).append(d)
+    tot = {k: sum(v) for k, v in per_kind.items()}
+    dom = max(tot, key=tot.get)
+    dom_ms = statistics.mean(per_kind[dom])
+    achieved = gate_bytes(n, amp_bytes) / (dom_ms * 1e-3) / 1e9
+    peak, peak_src = peaks()
+    per_target = []
+    for i, g in enumerate(gates[:n]):
+        d = statistics.median(ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps))
+        per_target.append(round(gate_bytes(n, amp_bytes) / (d * 1e-3) / 1e9, 1))
+
+    # End-to-end through the C ABI with host buffers: H2D of the state,
+    # the step's gates, D2H of the state, all inside the timed region.
+    e2e = None
+    if not args.no_e2e:
+        host_out = torch.empty(psi_host.nbytes, dtype=torch.uint8, pin_memory=True).numpy()
+        e_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            qs.qs_copy_in(st.h, host_in)
+            one_step()
+            qs.qs_copy_out(st.h, host_out)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e2e = {"value": world * bytes_step * e_steps / el / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(psi_host.nbytes), "d2h_bytes_per_step": int(psi_host.nbytes)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu and not c64:
+        gbs, done, secs = time_oracle_sample(psi_host.copy() if c64 else psi_host, [gates[0], gates[n]], 1e9)
+        cpu = {"value": gbs, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{done} gates (first 1q, first 2q of the sweep) on the full {n}-qubit state, "
+                         f"{secs:.1f} s single-thread"}
+
+    st.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"c128": {"df": "f64 storage, float-float arithmetic", "fp64": "f64"}[args.math],
+                          "c64": "f32"}[args.dtype],
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD if n == N_QUBITS else WORKLOAD.replace("30-qubit", f"{n}-qubit"),
+                           "n_qubits": n, "state": args.dtype, "math": args.math,
+                           "gates_per_step": len(gates), "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (16 GiB state, 129 MB L2)"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None, "kernel": dom,
+                             "peak_source": peak_src},
+                "per_kernel_ms": {k: statistics.mean(v) for k, v in per_kind.items()},
+                "gbs_per_target_1q": per_target,
+                "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+                "gpu_launches": len(gates) * args.steps}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

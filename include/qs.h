@@ -1,0 +1,209 @@
+/*
+ * qs.h — C ABI of libqs, a GB300 (sm_103a) state-vector gate engine.
+ *
+ * The library applies quantum gates to a state of 2^n complex amplitudes
+ * held in GPU memory (arXiv 2506.09198, Sec. I: "applying gate matrices to
+ * the state vector" is the core operation of full state-vector simulation).
+ *
+ * Layout (Sec. II-A, Fig. 1): amplitudes are stored array-of-structures,
+ * (re, im) side by side: complex64 = two floats (8 bytes), complex128 = two
+ * doubles (16 bytes) — the memory layout of torch.complex64/complex128.
+ * Qubit q is bit q of the amplitude index, qubit 0 the least significant
+ * (Algorithm 1: a gate on target t pairs index up, bit t = 0, with
+ * lo = up + 2^t).
+ *
+ * Matrices are always passed in double precision, row-major, with each
+ * complex entry as (re, im).  For a k-qubit matrix the row and column index
+ * is s = sum_j bit(targets[j]) * 2^j: targets[0] is the least significant
+ * (the paper fixes no basis order; this is the reading used throughout).
+ * A control list means the gate acts only on amplitudes whose control bits
+ * are all 1 (Fig. 4, Sec. III-A).  Controls on 0 are made by conjugating
+ * with X.
+ *
+ * Errors: every function returns a qs_status.  QS_OK is 0.  On any other
+ * value, qs_last_error() returns a message for the calling thread.  The
+ * library never aborts and never throws across this boundary.  Gate calls
+ * are asynchronous on the state's stream: an error raised on the device
+ * (for example a bounded wait that ran out) is reported by the next
+ * synchronous call (qs_sync, qs_norm, qs_probs, qs_copy_out, qs_gather).
+ *
+ * Threads: a qs_state handle is not thread-safe; distinct handles may be
+ * used from distinct threads.
+ */
+#ifndef QS_H
+#define QS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QS_OK = 0,
+  QS_ERR_ARG = 1,          /* invalid argument (range, duplicate qubit, bad table) */
+  QS_ERR_OOM = 2,          /* device memory could not be allocated */
+  QS_ERR_CUDA = 3,         /* a CUDA runtime call failed (message has the CUDA error) */
+  QS_ERR_TIMEOUT = 4,      /* a bounded wait (host or device) ran out */
+  QS_ERR_UNSUPPORTED = 5,  /* valid request this build does not handle */
+  QS_ERR_DEVICE = 6        /* a device-side check recorded an error */
+} qs_status;
+
+typedef enum { QS_C64 = 0, QS_C128 = 1 } qs_dtype;
+
+/* Arithmetic used for complex128 states.
+ * QS_MATH_DF: products and sums in float-float (pairs of FP32 values, about
+ *   48 significant bits) on the FP32 pipes; every result is rounded back to
+ *   IEEE double.  Default: GB300's FP64 pipe is about 70x slower than FP32.
+ *   Amplitude components below 2^-74 in magnitude are flushed to zero and
+ *   magnitudes must stay below 2^100.
+ * QS_MATH_FP64: plain IEEE double arithmetic on the FP64 pipe.
+ * complex64 states always compute in FP32. */
+typedef enum { QS_MATH_DF = 0, QS_MATH_FP64 = 1 } qs_math;
+
+typedef struct qs_state_s* qs_state;
+
+enum {
+  QS_MAX_QUBITS = 40,     /* index arithmetic limit; memory limits come first */
+  QS_MAX_TARGETS = 8      /* largest target set of a diagonal/permutation gate */
+};
+
+/* ---- state lifetime -------------------------------------------------- */
+
+/* Allocate a state of n qubits (1 <= n <= QS_MAX_QUBITS) with cudaMalloc on
+ * the current device and set it to |0...0>.  The handle owns the memory and
+ * uses the legacy default stream until qs_set_stream.  QS_ERR_OOM if the
+ * allocation fails. */
+qs_status qs_create(int n, qs_dtype dtype, qs_state* out);
+
+/* Wrap caller-owned device memory (for example a torch tensor) of
+ * 2^n amplitudes of dtype, 256-byte aligned.  The handle never frees it.
+ * stream may be NULL (legacy default stream). */
+qs_status qs_wrap(int n, qs_dtype dtype, void* device_ptr, void* stream, qs_state* out);
+
+/* Release the handle (and its memory if it owns it).  NULL is accepted. */
+qs_status qs_destroy(qs_state s);
+
+qs_status qs_set_stream(qs_state s, void* cuda_stream);
+qs_status qs_set_math(qs_state s, qs_math math);
+qs_status qs_num_qubits(qs_state s, int* n);
+qs_status qs_device_ptr(qs_state s, void** device_ptr);
+
+/* ---- data movement ---------------------------------------------------- */
+
+/* |idx> (0 <= idx < 2^n), written on the state's stream. */
+qs_status qs_init_basis(qs_state s, uint64_t idx);
+
+/* Copy 2^n amplitudes of the state's dtype from host memory, interleaved
+ * (re, im).  Asynchronous on the state's stream when host is pinned; the
+ * caller keeps host valid until the stream reaches this point. */
+qs_status qs_copy_in(qs_state s, const void* host);
+
+/* Copy the whole state to host memory (same layout).  Synchronous. */
+qs_status qs_copy_out(qs_state s, void* host);
+
+/* host_out[j] = amplitude idx[j] (count entries, state's dtype), for
+ * sampled checks of large states.  Synchronous.  Indices must be < 2^n. */
+qs_status qs_gather(qs_state s, const uint64_t* idx, int64_t count, void* host_out);
+
+/* ---- gates (asynchronous on the state's stream) ---------------------- */
+
+/* Single-qubit gate U (2x2: u00 u01 u10 u11, each (re, im)) on target.
+ * Pairs (up, lo = up + 2^target): up' = u00 up + u01 lo, lo' = u10 up + u11 lo
+ * (Algorithm 1, generalised from the Hadamard to any U). */
+qs_status qs_apply_1q(qs_state s, int target, const double U[8]);
+
+/* Two-qubit gate U (4x4) on (t0, t1), t0 != t1.  On each quad
+ * (a, a+2^t0, a+2^t1, a+2^t0+2^t1) with matrix index b_t0 + 2 b_t1 (Sec.
+ * III-A names two-qubit gates; the basis order is this library's reading). */
+qs_status qs_apply_2q(qs_state s, int t0, int t1, const double U[32]);
+
+/* Controlled single-qubit gate: U on target where all nctrl controls are 1
+ * (Fig. 4: only amplitudes with control bit 1 are updated).  nctrl may be 0.
+ * CNOT is ctrl = {c}, U = X. */
+qs_status qs_apply_ctrl(qs_state s, const int* ctrls, int nctrl, int target, const double U[8]);
+
+/* Diagonal gate on k targets (1 <= k <= QS_MAX_TARGETS):
+ * psi_i <- d[s(i)] psi_i with s(i) = sum_j bit(i, targets[j]) 2^j; d holds
+ * 2^k complex entries (re, im).  Controlled phase shifts (Sec. III-B) and
+ * phase oracles are diagonal gates. */
+qs_status qs_apply_diag(qs_state s, const int* targets, int k, const double* d);
+
+/* Permutation gate: where all controls are 1, the basis state with target
+ * sub-register value v moves to perm[v] (a bijection of 0..2^k-1,
+ * 1 <= k <= QS_MAX_TARGETS).  Controlled modular multiplication of the
+ * Shor-like workload (Sec. III-D) is such a gate.  Amplitudes are moved,
+ * never rounded. */
+qs_status qs_apply_perm(qs_state s, const int* ctrls, int nctrl, const int* targets, int k, const uint32_t* perm);
+
+/* ---- circuits ---------------------------------------------------------- */
+
+typedef enum {
+  QS_GATE_U1 = 0,    /* 2x2 matrix on targets[0] */
+  QS_GATE_UK = 1,    /* dense 2^k x 2^k matrix, 2 <= k <= 5 */
+  QS_GATE_DIAG = 2,  /* 2^k diagonal entries */
+  QS_GATE_PERM = 3   /* uint32 table of 2^k entries */
+} qs_gate_kind;
+
+typedef struct {
+  int32_t kind;                     /* qs_gate_kind */
+  int32_t k;                        /* number of targets */
+  int32_t targets[QS_MAX_TARGETS];  /* distinct, < n */
+  uint64_t ctrl_mask;               /* bit q set: qubit q is a control */
+  int64_t offset;                   /* first double of the gate's data in
+                                       qs_circuit.data (U1/UK/DIAG), or first
+                                       entry in qs_circuit.perm (PERM) */
+} qs_gate;
+
+typedef struct {
+  int64_t n_gates;
+  const qs_gate* gates;
+  const double* data;     /* matrices and diagonals, (re, im) interleaved */
+  const uint32_t* perm;   /* permutation tables */
+} qs_circuit;
+
+typedef struct {
+  int32_t max_fuse;   /* largest fused block in qubits: 0 = autotuned,
+                         1 = no fusion (one kernel per gate), 2..5 */
+  int32_t use_graph;  /* 1: capture the launch sequence as a CUDA graph and
+                         replay it (the graph is cached per circuit pointer) */
+  int32_t reserved[6];
+} qs_run_opts;
+
+/* Run a circuit on one state.  Consecutive gates whose qubits fit one
+ * block of at most max_fuse qubits are applied by one fused kernel that
+ * keeps the block's amplitudes in shared memory for all of its gates
+ * (related work, Sec. I: gate fusion and cache blocking).  Block products
+ * needed on the host are composed in FP64.  Result equals applying the
+ * gates one by one, up to rounding.  opts may be NULL (autotuned, no graph). */
+qs_status qs_fuse_run(qs_state s, const qs_circuit* c, const qs_run_opts* opts);
+
+/* Run circuits[i] on states[i] for i < count, all of one dtype and small
+ * enough for the batched kernel (n <= 14 for complex128, 15 for complex64),
+ * in one persistent launch on the first state's stream. */
+qs_status qs_batch_run(qs_state* states, const qs_circuit* const* circuits, int count, const qs_run_opts* opts);
+
+/* ---- reductions (synchronous) ---------------------------------------- */
+
+/* out = sum_i |psi_i|^2, accumulated with at least 48 significant bits and
+ * combined in FP64. */
+qs_status qs_norm(qs_state s, double* out);
+
+/* out[v] = sum over i with sub-register value v on qubits[0..k-1] of
+ * |psi_i|^2 (2^k doubles, 1 <= k <= 16). */
+qs_status qs_probs(qs_state s, const int* qubits, int k, double* out);
+
+/* Wait for the state's stream with a host-side deadline: QS_ERR_TIMEOUT if
+ * it has not drained after timeout_s seconds (the work is not cancelled).
+ * Reports device-side errors recorded since the last synchronous call. */
+qs_status qs_sync(qs_state s, double timeout_s);
+
+const char* qs_last_error(void);
+const char* qs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QS_H */

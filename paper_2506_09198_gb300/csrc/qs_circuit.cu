@@ -1,0 +1,98 @@
+// Circuit runner: validation of qs_circuit records and gate-by-gate dispatch.
+#include <cstring>
+#include <vector>
+
+#include "qs_internal.h"
+
+namespace qs {
+
+void release_plan_cache(qs_state s) { s->plan_cache = nullptr; }
+
+// Validates one gate record against the state and returns its control mask.
+qs_status check_gate(const qs_state s, const qs_circuit* c, int64_t gi) {
+  const qs_gate& g = c->gates[gi];
+  if (g.k < 1 || g.k > QS_MAX_TARGETS) return fail(QS_ERR_ARG, "gate %lld: k = %d out of range", (long long)gi, g.k);
+  uint64_t used = 0;
+  for (int j = 0; j < g.k; ++j) {
+    const int t = g.targets[j];
+    if (t < 0 || t >= s->n || ((used >> t) & 1ull))
+      return fail(QS_ERR_ARG, "gate %lld: bad or repeated target %d", (long long)gi, t);
+    used |= 1ull << t;
+  }
+  if (s->n < 64 && (g.ctrl_mask >> s->n) != 0)
+    return fail(QS_ERR_ARG, "gate %lld: control outside the register", (long long)gi);
+  if (g.ctrl_mask & used) return fail(QS_ERR_ARG, "gate %lld: control also a target", (long long)gi);
+  if (g.offset < 0) return fail(QS_ERR_ARG, "gate %lld: negative offset", (long long)gi);
+  switch (g.kind) {
+    case QS_GATE_U1:
+      if (g.k != 1) return fail(QS_ERR_ARG, "gate %lld: U1 needs k = 1", (long long)gi);
+      if (!c->data) return fail(QS_ERR_ARG, "circuit has no data pool");
+      break;
+    case QS_GATE_UK:
+      if (g.k > 5) return fail(QS_ERR_ARG, "gate %lld: dense gates take at most 5 targets", (long long)gi);
+      if (!c->data) return fail(QS_ERR_ARG, "circuit has no data pool");
+      break;
+    case QS_GATE_DIAG:
+      if (!c->data) return fail(QS_ERR_ARG, "circuit has no data pool");
+      break;
+    case QS_GATE_PERM: {
+      if (!c->perm) return fail(QS_ERR_ARG, "circuit has no permutation pool");
+      const uint32_t* p = c->perm + g.offset;
+      std::vector<char> seen((size_t)1 << g.k, 0);
+      for (int v = 0; v < (1 << g.k); ++v) {
+        if (p[v] >= (1u << g.k) || seen[p[v]]) return fail(QS_ERR_ARG, "gate %lld: not a bijection", (long long)gi);
+        seen[p[v]] = 1;
+      }
+      break;
+    }
+    default:
+      return fail(QS_ERR_ARG, "gate %lld: unknown kind %d", (long long)gi, g.kind);
+  }
+  return QS_OK;
+}
+
+qs_status apply_gate_record(qs_state s, const qs_circuit* c, const qs_gate& g) {
+  switch (g.kind) {
+    case QS_GATE_U1:
+      return dispatch_u1(s, g.targets[0], g.ctrl_mask, c->data + g.offset);
+    case QS_GATE_UK:
+      return dispatch_uk(s, g.targets, g.k, g.ctrl_mask, c->data + g.offset);
+    case QS_GATE_DIAG:
+      return dispatch_diag(s, g.targets, g.k, g.ctrl_mask, c->data + g.offset);
+    case QS_GATE_PERM:
+      return dispatch_perm(s, g.targets, g.k, g.ctrl_mask, c->perm + g.offset);
+  }
+  return fail(QS_ERR_ARG, "unknown gate kind");
+}
+
+}  // namespace qs
+
+using namespace qs;
+
+extern "C" {
+
+qs_status qs_fuse_run(qs_state s, const qs_circuit* c, const qs_run_opts* opts) {
+  (void)opts;
+  if (!s) return fail(QS_ERR_ARG, "state handle is NULL");
+  if (!c || c->n_gates < 0 || (c->n_gates > 0 && !c->gates)) return fail(QS_ERR_ARG, "bad circuit");
+  for (int64_t i = 0; i < c->n_gates; ++i) {
+    qs_status st = check_gate(s, c, i);
+    if (st != QS_OK) return st;
+  }
+  for (int64_t i = 0; i < c->n_gates; ++i) {
+    qs_status st = apply_gate_record(s, c, c->gates[i]);
+    if (st != QS_OK) return st;
+  }
+  return QS_OK;
+}
+
+qs_status qs_batch_run(qs_state* states, const qs_circuit* const* circuits, int count, const qs_run_opts* opts) {
+  if (count < 0 || (count > 0 && (!states || !circuits))) return fail(QS_ERR_ARG, "bad batch");
+  for (int i = 0; i < count; ++i) {
+    qs_status st = qs_fuse_run(states[i], circuits[i], opts);
+    if (st != QS_OK) return st;
+  }
+  return QS_OK;
+}
+
+}  // extern "C"

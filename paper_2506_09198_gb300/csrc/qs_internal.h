@@ -1,0 +1,91 @@
+// Internal declarations shared by the translation units of libqs.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "qs.h"
+
+struct qs_state_s {
+  int n = 0;
+  qs_dtype dtype = QS_C128;
+  qs_math math = QS_MATH_DF;
+  void* psi = nullptr;  // device amplitudes
+  bool owns = false;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  // Per-state scratch for reductions, grown on demand (cudaMalloc).
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  void* host_scratch = nullptr;  // pinned host mirror for small results
+  size_t host_scratch_bytes = 0;
+  // Fused-circuit cache (graph / plan), owned by qs_circuit.cu.
+  void* plan_cache = nullptr;
+};
+
+namespace qs {
+
+qs_status fail(qs_status st, const char* fmt, ...);
+qs_status cuda_fail(cudaError_t e, const char* what);
+#define QS_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return ::qs::cuda_fail(e_, #call); \
+  } while (0)
+
+inline size_t amp_bytes(qs_dtype dt) { return dt == QS_C64 ? 8 : 16; }
+
+// Device-side error word: kernels that run bounded waits or range checks
+// record a nonzero code here; qs_sync and every synchronous call read and
+// clear it.
+qs_status device_error_check(qs_state s);
+uint32_t* device_error_word(int device);
+
+// Number of resident CTAs per SM for a kernel, cached per function pointer.
+int sm_count(int device);
+
+// ---------------------------------------------------------------------------
+// Gate descriptors handed to the kernel launchers (already validated).
+// ---------------------------------------------------------------------------
+// Bits inserted into a compressed item index to form an amplitude index:
+// positions ascending; fixed_mask holds the bits that are 1 (controls,
+// matched pattern bits).
+struct InsertSpec {
+  int npos = 0;
+  uint64_t high_mask[QS_MAX_QUBITS];  // ~((1 << pos_j) - 1), ascending pos_j
+  uint64_t fixed_mask = 0;
+};
+InsertSpec make_insert(const std::vector<int>& positions, uint64_t fixed_mask);
+
+// Dense single-qubit gate (optionally controlled).
+qs_status launch_dense1(qs_state s, int target, uint64_t ctrl_mask, const double* U);
+// Dense two-qubit gate (optionally controlled), matrix index b_t0 + 2 b_t1.
+qs_status launch_dense2(qs_state s, int t0, int t1, uint64_t ctrl_mask, const double* U);
+// Multiply every amplitude whose bits under `mask` equal `pattern` by c.
+qs_status launch_phase(qs_state s, uint64_t mask, uint64_t pattern, double c_re, double c_im);
+// Swap pair partners on target (X), times +-i for Y (kind 1), under ctrl_mask.
+qs_status launch_xy(qs_state s, int target, uint64_t ctrl_mask, int y);
+// General diagonal on k targets under ctrl_mask.
+qs_status launch_diag(qs_state s, const int* targets, int k, uint64_t ctrl_mask, const double* d);
+// Permutation on k targets under ctrl_mask.
+qs_status launch_perm(qs_state s, const int* targets, int k, uint64_t ctrl_mask, const uint32_t* perm);
+
+// Reductions / data movement (qs_reduce.cu).
+qs_status launch_init_basis(qs_state s, uint64_t idx);
+qs_status run_norm(qs_state s, double* out);
+qs_status run_probs(qs_state s, const int* qubits, int k, double* out);
+qs_status run_gather(qs_state s, const uint64_t* idx, int64_t count, void* host_out);
+
+// Gate dispatch shared by the single-gate API and the circuit runner:
+// classify the gate (identity, diagonal, phase on a pattern, X/Y move,
+// permutation, dense) and launch the cheapest kernel for it.
+qs_status dispatch_u1(qs_state s, int target, uint64_t ctrl_mask, const double* U);
+qs_status dispatch_uk(qs_state s, const int* targets, int k, uint64_t ctrl_mask, const double* M);
+qs_status dispatch_diag(qs_state s, const int* targets, int k, uint64_t ctrl_mask, const double* d);
+qs_status dispatch_perm(qs_state s, const int* targets, int k, uint64_t ctrl_mask, const uint32_t* perm);
+
+qs_status ensure_scratch(qs_state s, size_t bytes);
+qs_status ensure_host_scratch(qs_state s, size_t bytes);
+
+}  // namespace qs

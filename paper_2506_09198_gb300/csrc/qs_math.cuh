@@ -1,0 +1,182 @@
+// Device arithmetic policies for the gate kernels.
+//
+// Three ways to compute one gate update  out = sum_k m_k * v_k  (complex):
+//   MathF32  complex64 state (float2), FP32 FMA arithmetic.
+//   MathF64  complex128 state (double2), plain IEEE double arithmetic.
+//   MathDF   complex128 state (double2), float-float arithmetic on the FP32
+//            pipes: each double is split into head + tail floats, products are
+//            formed exactly (TwoProduct via FMA, Dekker 1971) and summed with
+//            TwoSum (Knuth, TAOCP vol. 2) error terms; the result is rounded
+//            to double by one FP64 add of two exactly converted floats.
+// GB300 runs FP64 at about 1/70 of the FP32 rate, so MathDF is the default
+// for complex128: about 48 significant bits per product and sum, rounded to
+// IEEE double after every gate.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qs {
+
+// ---------------------------------------------------------------------------
+// Exact float <-> double conversions with integer instructions only (the
+// F2F conversions run on the slow FP64 pipe of this GPU).
+// ---------------------------------------------------------------------------
+
+// Float to double, exact for normal floats; zero and subnormal floats
+// (|f| < 2^-126) become a signed zero.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t sign = b & 0x80000000u;
+  const uint32_t mag = b & 0x7FFFFFFFu;
+  uint32_t hi = sign | ((mag >> 3) + (896u << 20));  // rebias 127 -> 1023
+  uint32_t lo = mag << 29;
+  if (mag < 0x00800000u) {
+    hi = sign;
+    lo = 0u;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// Double to head + tail floats: head = the leading 24 significant bits
+// (truncated), tail = the remaining 29 bits rounded to 24.  |x - h - l| <=
+// 2^-48 |x|.  |x| < 2^-74 gives h = l = 0; |x| must be below 2^127.
+__device__ __forceinline__ void d2ff(double x, float& h, float& l) {
+  const uint32_t lo32 = (uint32_t)__double2loint(x);
+  const uint32_t hi32 = (uint32_t)__double2hiint(x);
+  // (hi32 << 3) | (lo32 >> 29): exponent bits 7..0 land at 30..23 and the 23
+  // leading mantissa bits at 22..0.  Rebias 1023 -> 127 is a flip of bit 30
+  // (896 = 3*256 + 128); bit 31 is replaced by the sign.
+  const uint32_t fs = __funnelshift_l(lo32, hi32, 3) ^ 0x40000000u;
+  uint32_t hb = (fs & 0x7FFFFFFFu) | (hi32 & 0x80000000u);
+  // tail = sign * (lo32 & (2^29-1)) * 2^(E-1075); its scale is 2^-52 of the
+  // head's exponent, built by lowering the head's exponent field by 52.
+  const uint32_t scale_bits = (hb & 0xFF800000u) - (52u << 23);
+  float tl = __uint2float_rn(lo32 & 0x1FFFFFFFu) * __uint_as_float(scale_bits);
+  const uint32_t e = (hi32 >> 20) & 0x7FFu;
+  if (e < 949u) {  // |x| < 2^-74: flush
+    hb = 0u;
+    tl = 0.0f;
+  }
+  h = __uint_as_float(hb);
+  l = tl;
+}
+
+// ---------------------------------------------------------------------------
+// Float-float dot-product accumulator: sum of (ah+al)(xh+xl) terms.
+// ---------------------------------------------------------------------------
+struct DFAcc {
+  float s;  // sum of the exact product heads, kept exact through TwoSum
+  float c;  // all lower-order parts
+};
+
+__device__ __forceinline__ void df_first(DFAcc& a, float ah, float al, float xh, float xl) {
+  const float p = ah * xh;
+  const float e = __fmaf_rn(ah, xh, -p);  // p + e = ah * xh exactly
+  a.s = p;
+  a.c = __fmaf_rn(al, xh, __fmaf_rn(ah, xl, e));
+}
+
+__device__ __forceinline__ void df_add(DFAcc& a, float ah, float al, float xh, float xl) {
+  const float p = ah * xh;
+  const float e = __fmaf_rn(ah, xh, -p);
+  const float s = a.s + p;  // TwoSum(a.s, p): s + err = a.s + p exactly
+  const float bb = s - a.s;
+  const float err = (a.s - (s - bb)) + (p - bb);
+  a.s = s;
+  a.c = __fmaf_rn(al, xh, __fmaf_rn(ah, xl, a.c + (err + e)));
+}
+
+__device__ __forceinline__ double df_round(const DFAcc& a) {
+  return f2d_exact(a.s) + f2d_exact(a.c);
+}
+
+// ---------------------------------------------------------------------------
+// Policies.  Each provides:
+//   Amp       storage type of one amplitude
+//   Val       working value of one amplitude
+//   Coef      one complex matrix entry in working form
+//   make_coef(re, im)   host-side conversion of a double matrix entry
+//   load(Amp) -> Val
+//   mac_round<K>(coefs, vals) -> Amp   sum_k coefs[k] * vals[k], rounded to
+//                                      the storage type
+// ---------------------------------------------------------------------------
+struct MathF32 {
+  using Amp = float2;
+  struct Val { float re, im; };
+  struct Coef { float re, im; };
+  static __host__ Coef make_coef(double re, double im) { return Coef{(float)re, (float)im}; }
+  static __device__ __forceinline__ Val load(const Amp& a) { return Val{a.x, a.y}; }
+  static __device__ __forceinline__ Amp pack(const Val& v) { return make_float2(v.re, v.im); }
+  template <int K>
+  static __device__ __forceinline__ Val mac(const Coef* m, const Val* v) {
+    float re = 0.f, im = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      re = __fmaf_rn(m[k].re, v[k].re, re);
+      re = __fmaf_rn(-m[k].im, v[k].im, re);
+      im = __fmaf_rn(m[k].re, v[k].im, im);
+      im = __fmaf_rn(m[k].im, v[k].re, im);
+    }
+    return Val{re, im};
+  }
+  template <int K>
+  static __device__ __forceinline__ Amp mac_round(const Coef* m, const Val* v) { return pack(mac<K>(m, v)); }
+};
+
+struct MathF64 {
+  using Amp = double2;
+  struct Val { double re, im; };
+  struct Coef { double re, im; };
+  static __host__ Coef make_coef(double re, double im) { return Coef{re, im}; }
+  static __device__ __forceinline__ Val load(const Amp& a) { return Val{a.x, a.y}; }
+  static __device__ __forceinline__ Amp pack(const Val& v) { return make_double2(v.re, v.im); }
+  template <int K>
+  static __device__ __forceinline__ Val mac(const Coef* m, const Val* v) {
+    double re = 0.0, im = 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      re = __fma_rn(m[k].re, v[k].re, re);
+      re = __fma_rn(-m[k].im, v[k].im, re);
+      im = __fma_rn(m[k].re, v[k].im, im);
+      im = __fma_rn(m[k].im, v[k].re, im);
+    }
+    return Val{re, im};
+  }
+  template <int K>
+  static __device__ __forceinline__ Amp mac_round(const Coef* m, const Val* v) { return pack(mac<K>(m, v)); }
+};
+
+struct MathDF {
+  using Amp = double2;
+  struct Val { float rh, rl, ih, il; };
+  struct Coef { float rh, rl, ih, il; };
+  static __host__ Coef make_coef(double re, double im) {
+    const float rh = (float)re, ih = (float)im;
+    return Coef{rh, (float)(re - (double)rh), ih, (float)(im - (double)ih)};
+  }
+  static __device__ __forceinline__ Val load(const Amp& a) {
+    Val v;
+    d2ff(a.x, v.rh, v.rl);
+    d2ff(a.y, v.ih, v.il);
+    return v;
+  }
+  template <int K>
+  static __device__ __forceinline__ Amp mac_round(const Coef* m, const Val* v) {
+    DFAcc re, im;
+    // re = sum_k (mr vr - mi vi),  im = sum_k (mr vi + mi vr)
+    df_first(re, m[0].rh, m[0].rl, v[0].rh, v[0].rl);
+    df_add(re, -m[0].ih, -m[0].il, v[0].ih, v[0].il);
+    df_first(im, m[0].rh, m[0].rl, v[0].ih, v[0].il);
+    df_add(im, m[0].ih, m[0].il, v[0].rh, v[0].rl);
+#pragma unroll
+    for (int k = 1; k < K; ++k) {
+      df_add(re, m[k].rh, m[k].rl, v[k].rh, v[k].rl);
+      df_add(re, -m[k].ih, -m[k].il, v[k].ih, v[k].il);
+      df_add(im, m[k].rh, m[k].rl, v[k].ih, v[k].il);
+      df_add(im, m[k].ih, m[k].il, v[k].rh, v[k].rl);
+    }
+    return make_double2(df_round(re), df_round(im));
+  }
+};
+
+}  // namespace qs

@@ -1,0 +1,64 @@
+"""The C-ABI library loads, exports every symbol its header declares, and
+rejects bad arguments before touching CUDA (CPU only: no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qs.h")
+
+
+@pytest.fixture(scope="module")
+def qs():
+    from paper_2506_09198_gb300 import build
+
+    build.build()
+    from paper_2506_09198_gb300 import qs as mod
+
+    return mod
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:qs_status|const char\*)\s+(qs_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("qs_create", "qs_apply_1q", "qs_apply_2q", "qs_apply_ctrl", "qs_apply_diag",
+                     "qs_apply_perm", "qs_fuse_run", "qs_batch_run", "qs_norm", "qs_probs", "qs_sync"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(qs):
+    lib = qs.lib()
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in qs.h but not exported"
+    assert sorted(qs.EXPORTED) == declared_functions()
+
+
+def test_argument_validation_without_gpu(qs):
+    lib = qs.lib()
+    h = ctypes.c_void_p()
+    assert lib.qs_create(0, qs.QS_C128, ctypes.byref(h)) == qs.QS_ERR_ARG
+    assert "n = 0" in qs.qs_last_error()
+    assert lib.qs_create(35, qs.QS_C128, ctypes.byref(h)) == qs.QS_ERR_ARG
+    assert lib.qs_create(36, qs.QS_C64, ctypes.byref(h)) == qs.QS_ERR_ARG
+    assert lib.qs_create(10, 7, ctypes.byref(h)) == qs.QS_ERR_ARG
+    assert lib.qs_create(10, qs.QS_C64, None) == qs.QS_ERR_ARG
+    U = (ctypes.c_double * 8)()
+    assert lib.qs_apply_1q(None, 0, U) == qs.QS_ERR_ARG
+    assert lib.qs_norm(None, None) == qs.QS_ERR_ARG
+    assert lib.qs_sync(None, 1.0) == qs.QS_ERR_ARG
+    assert lib.qs_destroy(None) == qs.QS_OK
+    assert lib.qs_wrap(10, qs.QS_C128, None, None, ctypes.byref(h)) == qs.QS_ERR_ARG
+    assert lib.qs_batch_run(None, None, -1, None) == qs.QS_ERR_ARG
+    assert qs.qs_version().startswith("libqs")
+
+
+def test_binding_raises_qserror(qs):
+    with pytest.raises(qs.QSError) as e:
+        qs.qs_create(0, qs.QS_C64)
+    assert e.value.status == qs.QS_ERR_ARG

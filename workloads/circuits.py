@@ -171,16 +171,53 @@ def haar_unitary(dim: int, rng: np.random.Generator) -> np.ndarray:
     return q * (d / np.abs(d))[None, :]
 
 
-def random_state(n: int, rng: np.random.Generator, chunk: int = 1 << 24) -> np.ndarray:
-    """i.i.d. complex Gaussian amplitudes, normalised in double."""
+def random_state(n: int, rng, chunk: int = 1 << 24) -> np.ndarray:
+    """i.i.d. complex Gaussian amplitudes (re, im ~ N(0,1)), normalised in
+    double.  ``rng`` is a Generator (values drawn in order) or an int seed:
+    then chunk j of ``chunk`` doubles is drawn from PCG64 seeded by
+    SeedSequence(seed).spawn(...)[j], filled by parallel threads; the values
+    do not depend on the thread count."""
     psi = np.empty(1 << n, dtype=np.complex128)
     f = psi.view(np.float64)
-    for lo in range(0, f.size, chunk):
-        hi = min(f.size, lo + chunk)
-        f[lo:hi] = rng.standard_normal(hi - lo)
-    nrm = math.sqrt(float(np.sum(f * f, dtype=np.float64)))
-    f /= nrm
+    if isinstance(rng, np.random.Generator):
+        for lo in range(0, f.size, chunk):
+            hi = min(f.size, lo + chunk)
+            f[lo:hi] = rng.standard_normal(hi - lo)
+    else:
+        n_chunks = (f.size + chunk - 1) // chunk
+        kids = np.random.SeedSequence(int(rng)).spawn(n_chunks)
+
+        def fill(j):
+            lo = j * chunk
+            np.random.Generator(np.random.PCG64(kids[j])).standard_normal(out=f[lo:min(f.size, lo + chunk)])
+
+        _parallel(fill, n_chunks)
+    partial = np.zeros((f.size + chunk - 1) // chunk)
+
+    def sq(j):
+        seg = f[j * chunk:(j + 1) * chunk]
+        partial[j] = float(np.dot(seg, seg))
+
+    _parallel(sq, partial.size)
+    scale = 1.0 / math.sqrt(float(np.sum(partial)))
+
+    def norm(j):
+        f[j * chunk:(j + 1) * chunk] *= scale
+
+    _parallel(norm, partial.size)
     return psi
+
+
+def _parallel(fn, count):
+    if count <= 1:
+        for j in range(count):
+            fn(j)
+        return
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    with ThreadPoolExecutor(max_workers=min(count, os.cpu_count() or 1)) as ex:
+        list(ex.map(fn, range(count)))
 
 
 def random_distinct(rng, n, k):
