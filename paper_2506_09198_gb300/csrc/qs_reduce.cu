@@ -198,11 +198,13 @@ qs_status launch_init_basis(qs_state s, uint64_t idx) {
 qs_status run_gather(qs_state s, const uint64_t* idx, int64_t count, void* host_out) {
   if (count == 0) return QS_OK;
   const size_t ab = amp_bytes(s->dtype);
-  const size_t need = (size_t)count * (sizeof(uint64_t) + ab);
+  // Output block starts on a 256-byte boundary (16-byte amplitude stores).
+  const size_t out_off = ((size_t)count * sizeof(uint64_t) + 255) & ~(size_t)255;
+  const size_t need = out_off + (size_t)count * ab;
   qs_status st = ensure_scratch(s, need);
   if (st != QS_OK) return st;
   uint64_t* didx = (uint64_t*)s->scratch;
-  void* dout = (char*)s->scratch + (size_t)count * sizeof(uint64_t);
+  void* dout = (char*)s->scratch + out_off;
   QS_CUDA(cudaMemcpyAsync(didx, idx, (size_t)count * sizeof(uint64_t), cudaMemcpyHostToDevice, s->stream));
   const unsigned grid = (unsigned)((count + 255) / 256 < 4096 ? (count + 255) / 256 : 4096);
   if (s->dtype == QS_C64)
