@@ -194,6 +194,27 @@ qs_status qs_norm(qs_state s, double* out);
  * |psi_i|^2 (2^k doubles, 1 <= k <= 16). */
 qs_status qs_probs(qs_state s, const int* qubits, int k, double* out);
 
+/* Marginal probabilities like qs_probs, or the norm with k = 0, for callers
+ * that cannot allocate memory.  The paper has no counterpart: this is a
+ * deployment variant.  qs_probs grows a per-state scratch buffer with
+ * cudaMalloc (and a pinned host buffer); callers whose device memory belongs
+ * to another allocator, that must not pay an allocation or the device-wide
+ * synchronisation of a later cudaFree inside a latency-critical loop, or that
+ * hold only raw device pointers, call this instead.  It allocates nothing:
+ * its scratch is a fixed array of 2^16 doubles (512 KiB) inside the library's
+ * device image, held by every GPU that loads the library until exit.
+ *   device_state  2^n amplitudes of dtype, device memory, 16-byte aligned
+ *   qubits, k     0 <= k <= min(16, n) distinct qubits (k = 0: out[0] = norm)
+ *   device_out    2^k doubles of device memory (8-byte aligned), written
+ *                 asynchronously on stream (NULL: legacy default stream)
+ * Larger k is rejected with QS_ERR_ARG.  The first call on each device looks
+ * up the scratch address on the current device; make it before any stream
+ * capture.  All calls share the scratch: calls that overlap on the GPU race,
+ * so serialise them.  The scratch keeps the last call's contents; every slot
+ * a call reads is written by that call first. */
+qs_status qs_probs_noalloc(const void* device_state, int n, qs_dtype dtype, const int* qubits, int k,
+                           double* device_out, void* stream);
+
 /* Wait for the state's stream with a host-side deadline: QS_ERR_TIMEOUT if
  * it has not drained after timeout_s seconds (the work is not cancelled).
  * Reports device-side errors recorded since the last synchronous call. */

@@ -184,6 +184,51 @@ qs_status run_probs(qs_state s, const int* qubits, int k, double* out) {
 
 qs_status run_norm(qs_state s, double* out) { return run_probs(s, nullptr, 0, out); }
 
+// Same partial-sum and row-sum kernels as run_probs, writing into buffers the
+// caller provides: partial (partial_cap doubles) and dout (2^k doubles, device
+// memory).  Allocates nothing on host or device and does not synchronise.
+qs_status launch_probs_into(const void* psi, int n, qs_dtype dtype, const int* qubits, int k, double* partial,
+                            uint64_t partial_cap, double* dout, cudaStream_t stream, int device) {
+  MeasSpec m;
+  std::memset(&m, 0, sizeof(m));
+  int pos[16];
+  for (int j = 0; j < k; ++j) pos[j] = qubits[j];
+  for (int a = 1; a < k; ++a)  // insertion sort, ascending
+    for (int b = a; b > 0 && pos[b - 1] > pos[b]; --b) {
+      const int t = pos[b];
+      pos[b] = pos[b - 1];
+      pos[b - 1] = t;
+    }
+  m.npos = k;
+  for (int j = 0; j < k; ++j) m.high_mask[j] = ~((1ull << pos[j]) - 1ull);
+  m.k = k;
+  for (int j = 0; j < k; ++j) m.qubits[j] = qubits[j];
+  const int nfree = n - k;
+  const uint64_t nout = 1ull << k;
+  if (partial_cap < nout) return fail(QS_ERR_ARG, "scratch holds %llu partials, %llu outcomes requested",
+                                      (unsigned long long)partial_cap, (unsigned long long)nout);
+  const uint64_t want = (uint64_t)sm_count(device) * 8;
+  uint64_t nchunks = 1;
+  int log_nchunks = 0;
+  while (nchunks * nout < want && nchunks * 2 <= (1ull << nfree) && nchunks < 65536 &&
+         nchunks * 2 * nout <= partial_cap) {
+    nchunks *= 2;
+    ++log_nchunks;
+  }
+  const uint64_t per_chunk = (1ull << nfree) / nchunks;
+  const unsigned grid = (unsigned)(nchunks * nout);
+  if (dtype == QS_C64) {
+    k_sq_partial<float2, 8><<<grid, kRThreads, 0, stream>>>((const float2*)psi, per_chunk, log_nchunks, m, partial);
+  } else {
+    k_sq_partial<double2, 4><<<grid, kRThreads, 0, stream>>>((const double2*)psi, per_chunk, log_nchunks, m,
+                                                               partial);
+  }
+  QS_CUDA(cudaGetLastError());
+  k_sum_rows<<<(unsigned)nout, kRThreads, 0, stream>>>(partial, (int)nchunks, dout);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
 qs_status launch_init_basis(qs_state s, uint64_t idx) {
   const size_t bytes = amp_bytes(s->dtype) << s->n;
   QS_CUDA(cudaMemsetAsync(s->psi, 0, bytes, s->stream));

@@ -79,6 +79,7 @@ _SIGS = {
     "qs_norm": [_P, _PD],
     "qs_probs": [_P, _PI, _I, _PD],
     "qs_sync": [_P, ctypes.c_double],
+    "qs_probs_noalloc": [_P, _I, _I, _PI, _I, _P, _P],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -219,6 +220,13 @@ def qs_probs(h, qubits) -> np.ndarray:
     out = np.zeros(1 << q.size, dtype=np.float64)
     _check(_lib.qs_probs(h, pq, q.size, out.ctypes.data_as(_PD)))
     return out
+
+
+def qs_probs_noalloc(device_state: int, n: int, dtype: int, qubits, device_out: int, stream: int = 0):
+    """No-allocation marginals (k = len(qubits), 0 for the norm) into 2^k
+    doubles of device memory at device_out, asynchronous on stream."""
+    q, pq = _i32(qubits)
+    _check(_lib.qs_probs_noalloc(_P(device_state), n, dtype, pq, q.size, _P(device_out), _P(stream or None)))
 
 
 def qs_sync(h, timeout_s: float = 60.0):
