@@ -146,36 +146,112 @@ struct MathF64 {
   static __device__ __forceinline__ Amp mac_round(const Coef* m, const Val* v) { return pack(mac<K>(m, v)); }
 };
 
+// ---------------------------------------------------------------------------
+// Packed FP32x2 arithmetic (sm_100+): one instruction computes two lanes, so
+// the real and imaginary channels of a complex dot product share each issue.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long f2_bits(float2 a) {
+  return ((unsigned long long)__float_as_uint(a.y) << 32) | __float_as_uint(a.x);
+}
+__device__ __forceinline__ float2 bits_f2(unsigned long long r) {
+  return make_float2(__uint_as_float((uint32_t)r), __uint_as_float((uint32_t)(r >> 32)));
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(d);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
+  return bits_f2(d);
+}
+
+// Float-float complex dot product on (re, im) channel pairs.
+//   A term multiplies (vr, vi) by (mr, mr); a B term multiplies the swapped
+//   value (vi, vr) by (-mi, mi): re += mr vr - mi vi, im += mr vi + mi vr.
+// Each vector term: exact product head (mul) and tail (fma against the
+// negated head), TwoSum of the head into S, every lower-order part into C.
+struct DF2Term {
+  float2 h, hn, l;  // coefficient head, negated head, tail (per channel)
+};
+
+struct DF2Acc {
+  float2 S, C;
+  __device__ __forceinline__ void first(const DF2Term& a, float2 xh, float2 xl) {
+    S = mul2(a.h, xh);
+    const float2 ne = fma2(a.hn, xh, S);  // S - a.h xh = -(product tail), exact
+    C = sub2(fma2(a.l, xh, mul2(a.h, xl)), ne);
+  }
+  __device__ __forceinline__ void add(const DF2Term& a, float2 xh, float2 xl) {
+    const float2 pn = mul2(a.hn, xh);     // -p
+    const float2 e = fma2(a.h, xh, pn);   // a.h xh - p, exact
+    const float2 s = sub2(S, pn);         // TwoSum(S, p)
+    const float2 bb = sub2(s, S);
+    const float2 t2 = sub2(S, sub2(s, bb));
+    const float2 err = sub2(t2, add2(pn, bb));  // (S - (s - bb)) + (p - bb)
+    C = add2(C, add2(err, e));
+    C = fma2(a.h, xl, C);
+    C = fma2(a.l, xh, C);
+    S = s;
+  }
+};
+
 struct MathDF {
   using Amp = double2;
-  struct Val { float rh, rl, ih, il; };
-  struct Coef { float rh, rl, ih, il; };
+  struct Val {
+    float2 h, l;    // (re, im) heads and tails
+    float2 hs, ls;  // the same, channels swapped (im, re)
+  };
+  struct Coef {
+    DF2Term a, b;   // A term (mr, mr) and B term (-mi, mi)
+  };
   static __host__ Coef make_coef(double re, double im) {
     const float rh = (float)re, ih = (float)im;
-    return Coef{rh, (float)(re - (double)rh), ih, (float)(im - (double)ih)};
+    const float rl = (float)(re - (double)rh), il = (float)(im - (double)ih);
+    Coef c;
+    c.a.h = make_float2(rh, rh);
+    c.a.hn = make_float2(-rh, -rh);
+    c.a.l = make_float2(rl, rl);
+    c.b.h = make_float2(-ih, ih);
+    c.b.hn = make_float2(ih, -ih);
+    c.b.l = make_float2(-il, il);
+    return c;
   }
   static __device__ __forceinline__ Val load(const Amp& a) {
     Val v;
-    d2ff(a.x, v.rh, v.rl);
-    d2ff(a.y, v.ih, v.il);
+    d2ff(a.x, v.h.x, v.l.x);
+    d2ff(a.y, v.h.y, v.l.y);
+    v.hs = make_float2(v.h.y, v.h.x);
+    v.ls = make_float2(v.l.y, v.l.x);
     return v;
   }
   template <int K>
-  static __device__ __forceinline__ Amp mac_round(const Coef* m, const Val* v) {
-    DFAcc re, im;
-    // re = sum_k (mr vr - mi vi),  im = sum_k (mr vi + mi vr)
-    df_first(re, m[0].rh, m[0].rl, v[0].rh, v[0].rl);
-    df_add(re, -m[0].ih, -m[0].il, v[0].ih, v[0].il);
-    df_first(im, m[0].rh, m[0].rl, v[0].ih, v[0].il);
-    df_add(im, m[0].ih, m[0].il, v[0].rh, v[0].rl);
+  static __device__ __forceinline__ DF2Acc mac(const Coef* m, const Val* v) {
+    DF2Acc acc;
+    acc.first(m[0].a, v[0].h, v[0].l);
+    acc.add(m[0].b, v[0].hs, v[0].ls);
 #pragma unroll
     for (int k = 1; k < K; ++k) {
-      df_add(re, m[k].rh, m[k].rl, v[k].rh, v[k].rl);
-      df_add(re, -m[k].ih, -m[k].il, v[k].ih, v[k].il);
-      df_add(im, m[k].rh, m[k].rl, v[k].ih, v[k].il);
-      df_add(im, m[k].ih, m[k].il, v[k].rh, v[k].rl);
+      acc.add(m[k].a, v[k].h, v[k].l);
+      acc.add(m[k].b, v[k].hs, v[k].ls);
     }
-    return make_double2(df_round(re), df_round(im));
+    return acc;
+  }
+  template <int K>
+  static __device__ __forceinline__ Amp mac_round(const Coef* m, const Val* v) {
+    const DF2Acc acc = mac<K>(m, v);
+    return make_double2(f2d_exact(acc.S.x) + f2d_exact(acc.C.x), f2d_exact(acc.S.y) + f2d_exact(acc.C.y));
   }
 };
 
