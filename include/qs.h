@@ -78,7 +78,7 @@ enum {
 qs_status qs_create(int n, qs_dtype dtype, qs_state* out);
 
 /* Wrap caller-owned device memory (for example a torch tensor) of
- * 2^n amplitudes of dtype, 256-byte aligned.  The handle never frees it.
+ * 2^n amplitudes of dtype, 16-byte aligned.  The handle never frees it.
  * stream may be NULL (legacy default stream). */
 qs_status qs_wrap(int n, qs_dtype dtype, void* device_ptr, void* stream, qs_state* out);
 
@@ -141,7 +141,9 @@ qs_status qs_apply_perm(qs_state s, const int* ctrls, int nctrl, const int* targ
 
 typedef enum {
   QS_GATE_U1 = 0,    /* 2x2 matrix on targets[0] */
-  QS_GATE_UK = 1,    /* dense 2^k x 2^k matrix, 2 <= k <= 5 */
+  QS_GATE_UK = 1,    /* 2^k x 2^k matrix: any for k <= 2; for 3 <= k <= 8 only
+                        diagonal or permutation matrices (QS_ERR_UNSUPPORTED
+                        otherwise) */
   QS_GATE_DIAG = 2,  /* 2^k diagonal entries */
   QS_GATE_PERM = 3   /* uint32 table of 2^k entries */
 } qs_gate_kind;
@@ -164,8 +166,10 @@ typedef struct {
 } qs_circuit;
 
 typedef struct {
-  int32_t max_fuse;   /* largest fused block in qubits: 0 = autotuned,
-                         1 = no fusion (one kernel per gate), 2..5 */
+  int32_t max_fuse;   /* fusion: 1 = none (one kernel per gate); 2..6 = most
+                         qubits above the resident low block that one fused
+                         block may span (the block's tile holds 2^max_fuse
+                         strided chunks); 0 = default (5) */
   int32_t use_graph;  /* 1: capture the launch sequence as a CUDA graph and
                          replay it (the graph is cached per circuit pointer) */
   int32_t reserved[6];

@@ -1,0 +1,453 @@
+// Batched execution of many independent states in one persistent launch.
+//
+// Every state's circuit is compiled on the host into fused blocks (the same
+// fuser and tile ops as qs_fuse_run, with no per-block size limits).  States
+// are ordered by estimated cost, largest first, and CTAs claim them from a
+// global counter, so uneven qubit counts balance across the 152 SMs.  A CTA
+// owns a claimed state until its circuit is done: a state no larger than one
+// tile is loaded into shared memory once, runs its whole circuit there and
+// is written back once; larger states stream through the CTA's tile ring
+// block after block (a block's stores complete before the next block's loads
+// start, since blocks overlap in memory).
+//
+// Roles inside a CTA are those of k_tile: a producer thread claims states,
+// issues the bulk copies and publishes a small descriptor per tile in shared
+// memory; eight consumer warps apply the ops.  Waits are bounded as in k_tile.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "qs_fuser.h"
+#include "qs_internal.h"
+#include "qs_tile_dev.cuh"
+
+namespace qs {
+
+qs_status check_gate(const qs_state s, const qs_circuit* c, int64_t gi);  // qs_circuit.cu
+
+struct BatchBlock {
+  int L, m, nops, pad;
+  uint32_t op0, coef0, perm0, pad2;
+  uint64_t n_tiles;
+  uint64_t base_high[kTileMaxHigh];
+  int8_t hq[kTileMaxHigh];
+};
+
+struct BatchState {
+  void* psi;
+  uint32_t block0, nblocks;
+};
+
+struct TileDesc {
+  uint32_t block;   // 0xFFFFFFFF: no more work
+  uint32_t pad;
+  uint64_t tau;
+};
+
+template <class TP>
+struct BatchArgs {
+  const BatchState* states;
+  const BatchBlock* blocks;
+  const TileOp* ops;
+  const typename TP::M::Coef* coefs;
+  const uint8_t* perm;
+  uint32_t n_states;
+  uint32_t* counter;  // next state to claim (zeroed before the launch)
+  uint32_t* err;
+};
+
+__device__ __forceinline__ uint64_t chunk_offset(const BatchBlock& b, uint32_t c) {
+  uint64_t off = 0;
+  for (int j = 0; j < b.m; ++j)
+    if ((c >> j) & 1u) off |= 1ull << b.hq[j];
+  return off;
+}
+
+template <class TP>
+__global__ void __launch_bounds__(kTileThreads, 2) k_batch(const BatchArgs<TP> a) {
+  using Glob = typename TP::Glob;
+  using Sm = typename TP::Sm;
+  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr uint32_t kMaxTileBytes = (uint32_t)sizeof(Glob) << TP::kTileLog;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kMaxTileBytes);
+  uint64_t* done = full + kStages;
+  TileDesc* desc = reinterpret_cast<TileDesc*>(done + kStages);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&done[s], kTileConsumers);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  if (tid >= kTileConsumers) {
+    // ---------------- producer ----------------
+    if (tid != kTileConsumers) return;
+    bool pending[kStages] = {false, false, false};
+    uint32_t pend_block[kStages], pend_j[kStages];
+    uint64_t pend_tau[kStages];
+    Glob* pend_psi[kStages];
+    uint32_t j = 0;
+    bool ok = true;
+    // Make stage s free: store the tile it holds once the consumers are done.
+    auto release = [&](int s) -> bool {
+      if (!pending[s]) return true;
+      if (!mbar_wait(&done[s], (pend_j[s] / kStages) & 1u, a.err)) return false;
+      const BatchBlock& b = a.blocks[pend_block[s]];
+      const uint32_t chunk_bytes = (uint32_t)sizeof(Glob) << b.L;
+      const uint64_t base = tile_base(pend_tau[s], b.L, b.m, b.base_high);
+      unsigned char* buf = smem + (size_t)s * kMaxTileBytes;
+      for (uint32_t c = 0; c < (1u << b.m); ++c)
+        bulk_store(pend_psi[s] + base + chunk_offset(b, c), buf + (size_t)c * chunk_bytes, chunk_bytes);
+      bulk_commit();
+      bulk_wait_read_all();
+      pending[s] = false;
+      return true;
+    };
+    auto drain = [&]() -> bool {
+      for (uint32_t jj = (j > (uint32_t)kStages ? j - kStages : 0u); jj < j; ++jj)
+        if (!release((int)(jj % kStages))) return false;
+      bulk_wait_all();
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      return true;
+    };
+    for (;;) {
+      const uint32_t si = atomicAdd(a.counter, 1u);
+      if (si >= a.n_states) break;
+      const BatchState st = a.states[si];
+      for (uint32_t bi = st.block0; bi < st.block0 + st.nblocks && ok; ++bi) {
+        // Blocks of one state overlap in memory: finish the previous block.
+        if (bi != st.block0 && !drain()) {
+          ok = false;
+          break;
+        }
+        const BatchBlock& b = a.blocks[bi];
+        const uint32_t chunk_bytes = (uint32_t)sizeof(Glob) << b.L;
+        const uint32_t tile_bytes = chunk_bytes << b.m;
+        for (uint64_t tau = 0; tau < b.n_tiles; ++tau, ++j) {
+          const int s = (int)(j % kStages);
+          if (!release(s)) {
+            ok = false;
+            break;
+          }
+          desc[s].block = bi;
+          desc[s].tau = tau;
+          pending[s] = true;
+          pend_block[s] = bi;
+          pend_j[s] = j;
+          pend_tau[s] = tau;
+          pend_psi[s] = reinterpret_cast<Glob*>(st.psi);
+          const uint64_t base = tile_base(tau, b.L, b.m, b.base_high);
+          unsigned char* buf = smem + (size_t)s * kMaxTileBytes;
+          mbar_expect_tx(&full[s], tile_bytes);
+          for (uint32_t c = 0; c < (1u << b.m); ++c)
+            bulk_load(buf + (size_t)c * chunk_bytes, reinterpret_cast<Glob*>(st.psi) + base + chunk_offset(b, c),
+                      chunk_bytes, &full[s]);
+        }
+      }
+      if (!ok) break;
+    }
+    if (ok) {
+      // End marker for the consumers, then store what is still in flight.
+      const int s = (int)(j % kStages);
+      ok = release(s);
+      if (ok) {
+        desc[s].block = 0xFFFFFFFFu;
+        mbar_arrive(&full[s]);
+        ok = drain();
+      }
+    }
+    if (!ok) {
+      // Let issued loads land before the CTA exits (bounded).
+      for (uint32_t jj = (j > (uint32_t)kStages ? j - kStages : 0u); jj < j; ++jj) {
+        const int s = (int)(jj % kStages);
+        const uint64_t t0 = global_ns();
+        while (!mbar_try(&full[s], (jj / kStages) & 1u) && global_ns() - t0 < kWaitNs) {
+        }
+      }
+      bulk_wait_all();
+    }
+    return;
+  }
+
+  // ---------------- consumers ----------------
+  for (uint32_t j = 0;; ++j) {
+    const int s = (int)(j % kStages);
+    const bool ok = mbar_wait(&full[s], (j / kStages) & 1u, a.err);
+    if (consumers_any(!ok)) break;
+    const TileDesc d = desc[s];
+    if (d.block == 0xFFFFFFFFu) break;
+    const BatchBlock& b = a.blocks[d.block];
+    const uint32_t tile_amps = 1u << (b.L + b.m);
+    Sm* t = reinterpret_cast<Sm*>(smem + (size_t)s * kMaxTileBytes);
+    if constexpr (!std::is_same<Glob, Sm>::value) {
+      for (uint32_t e = tid; e < tile_amps; e += kTileConsumers) t[e] = TP::to_sm(reinterpret_cast<Glob*>(t)[e]);
+      consumers_sync();
+    }
+    const uint64_t base = tile_base(d.tau, b.L, b.m, b.base_high);
+    const TileOp* ops = a.ops + b.op0;
+    const typename TP::M::Coef* coefs = a.coefs + b.coef0;
+    const uint8_t* perm = a.perm + b.perm0;
+    for (int o = 0; o < b.nops; ++o) {
+      const TileOp& op = ops[o];
+      if ((base & op.gmask) != op.gpat) continue;
+      apply_op<TP>(t, op, coefs, perm, tile_amps, base, tid);
+      consumers_sync();
+    }
+    if constexpr (!std::is_same<Glob, Sm>::value) {
+      for (uint32_t e = tid; e < tile_amps; e += kTileConsumers) reinterpret_cast<Glob*>(t)[e] = TP::from_sm(t[e]);
+    }
+    fence_async_smem();
+    mbar_arrive(&done[s]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host
+// ---------------------------------------------------------------------------
+namespace {
+
+using namespace fuser;
+
+struct BatchCache {
+  std::vector<const void*> key;  // states and circuit pointers of the cached batch
+  int dtype = -1, math = -1;
+  void* dev = nullptr;
+  size_t dev_bytes = 0;
+  size_t off_states = 0, off_blocks = 0, off_ops = 0, off_coefs = 0, off_perm = 0, off_counter = 0;
+  uint32_t n_states = 0;
+  cudaGraphExec_t graph = nullptr;
+  int grid = 0;
+  size_t smem = 0;
+};
+
+std::mutex g_batch_mu;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+template <class TP>
+qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int count, BatchCache* bc) {
+  using Coef = typename TP::M::Coef;
+  const int min_chunk = sizeof(typename TP::Glob) == 16 ? 3 : 4;
+  const Limits lim{1 << 20, 65535, 65535};
+  std::vector<BatchState> bstates(count);
+  std::vector<BatchBlock> blocks;
+  std::vector<TileOp> ops;
+  std::vector<Coef> coefs;
+  std::vector<uint8_t> perm;
+  std::vector<double> cost(count, 0.0);
+  BlockOut<Coef> bo;
+  for (int i = 0; i < count; ++i) {
+    const qs_state s = states[i];
+    const qs_circuit* c = circuits[i];
+    std::vector<FGate> gates;
+    gates.reserve((size_t)c->n_gates);
+    for (int64_t g = 0; g < c->n_gates; ++g) gates.push_back(normalise(c, c->gates[g]));
+    bstates[i].psi = s->psi;
+    bstates[i].block0 = (uint32_t)blocks.size();
+    std::vector<char> taken(gates.size(), 0);
+    size_t next = 0;
+    while (next < gates.size()) {
+      if (taken[next]) {
+        ++next;
+        continue;
+      }
+      Geom geom;
+      const std::vector<size_t> members =
+          choose_block(gates, taken, next, s->n, TP::kTileLog, kTileMaxHigh, min_chunk, lim, 1 << 16, &geom);
+      if (members.empty()) return fail(QS_ERR_UNSUPPORTED, "batch state %d: gate %zu fits no tile", i, next);
+      PlanBuilder<typename TP::M> pb(&bo, geom, lim);
+      size_t emitted = 0;
+      for (size_t idx : members) {
+        if (!pb.add(gates[idx])) break;
+        taken[idx] = 1;
+        ++emitted;
+      }
+      if (emitted == 0) return fail(QS_ERR_UNSUPPORTED, "batch state %d: gate %zu could not be placed", i, next);
+      if (bo.ops.empty()) continue;
+      BatchBlock b;
+      std::memset(&b, 0, sizeof(b));
+      b.L = geom.L;
+      b.m = geom.m;
+      b.nops = (int)bo.ops.size();
+      b.op0 = (uint32_t)ops.size();
+      b.coef0 = (uint32_t)coefs.size();
+      b.perm0 = (uint32_t)perm.size();
+      b.n_tiles = 1ull << (s->n - geom.L - geom.m);
+      for (int jq = 0; jq < geom.m; ++jq) {
+        b.base_high[jq] = ~((1ull << geom.hq[jq]) - 1ull);
+        b.hq[jq] = (int8_t)geom.hq[jq];
+      }
+      blocks.push_back(b);
+      ops.insert(ops.end(), bo.ops.begin(), bo.ops.end());
+      coefs.insert(coefs.end(), bo.coefs.begin(), bo.coefs.end());
+      perm.insert(perm.end(), bo.perm.begin(), bo.perm.end());
+      cost[i] += (double)(1ull << s->n) * (2.0 + (double)b.nops);
+    }
+    bstates[i].nblocks = (uint32_t)blocks.size() - bstates[i].block0;
+  }
+  // Largest estimated cost first.
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  std::vector<BatchState> sorted(count);
+  for (int i = 0; i < count; ++i) sorted[i] = bstates[order[i]];
+
+  size_t off = 0;
+  bc->off_states = off;
+  off = align_up(off + sorted.size() * sizeof(BatchState), 256);
+  bc->off_blocks = off;
+  off = align_up(off + blocks.size() * sizeof(BatchBlock), 256);
+  bc->off_ops = off;
+  off = align_up(off + ops.size() * sizeof(TileOp), 256);
+  bc->off_coefs = off;
+  off = align_up(off + coefs.size() * sizeof(Coef), 256);
+  bc->off_perm = off;
+  off = align_up(off + perm.size() + 1, 256);
+  bc->off_counter = off;
+  off = align_up(off + sizeof(uint32_t), 256);
+  if (bc->dev_bytes < off) {
+    if (bc->dev) {
+      cudaStreamSynchronize(states[0]->stream);
+      cudaFree(bc->dev);
+      bc->dev = nullptr;
+      bc->dev_bytes = 0;
+    }
+    QS_CUDA(cudaMalloc(&bc->dev, off));
+    bc->dev_bytes = off;
+  }
+  std::vector<unsigned char> host(off, 0);
+  std::memcpy(host.data() + bc->off_states, sorted.data(), sorted.size() * sizeof(BatchState));
+  std::memcpy(host.data() + bc->off_blocks, blocks.data(), blocks.size() * sizeof(BatchBlock));
+  std::memcpy(host.data() + bc->off_ops, ops.data(), ops.size() * sizeof(TileOp));
+  std::memcpy(host.data() + bc->off_coefs, coefs.data(), coefs.size() * sizeof(Coef));
+  if (!perm.empty()) std::memcpy(host.data() + bc->off_perm, perm.data(), perm.size());
+  QS_CUDA(cudaMemcpy(bc->dev, host.data(), off, cudaMemcpyHostToDevice));
+  bc->n_states = (uint32_t)count;
+  return QS_OK;
+}
+
+template <class TP>
+qs_status launch_batch(qs_state s0, BatchCache* bc, cudaStream_t stream) {
+  const size_t smem = kStages * ((size_t)sizeof(typename TP::Glob) << TP::kTileLog) + 2 * kStages * sizeof(uint64_t) +
+                      kStages * sizeof(TileDesc);
+  auto kern = k_batch<TP>;
+  QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTileThreads, smem) != cudaSuccess || occ < 1) occ = 1;
+  int grid = sm_count(s0->device) * occ;
+  if ((uint32_t)grid > bc->n_states) grid = (int)bc->n_states;
+  BatchArgs<TP> args;
+  unsigned char* base = (unsigned char*)bc->dev;
+  args.states = (const BatchState*)(base + bc->off_states);
+  args.blocks = (const BatchBlock*)(base + bc->off_blocks);
+  args.ops = (const TileOp*)(base + bc->off_ops);
+  args.coefs = (const typename TP::M::Coef*)(base + bc->off_coefs);
+  args.perm = base + bc->off_perm;
+  args.n_states = bc->n_states;
+  args.counter = (uint32_t*)(base + bc->off_counter);
+  args.err = device_error_word(s0->device);
+  if (!args.err) return fail(QS_ERR_CUDA, "device error word unavailable");
+  QS_CUDA(cudaMemsetAsync(args.counter, 0, sizeof(uint32_t), stream));
+  kern<<<grid, kTileThreads, smem, stream>>>(args);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+template <class TP>
+qs_status run_batch(qs_state* states, const qs_circuit* const* circuits, int count, const qs_run_opts* opts) {
+  qs_state s0 = states[0];
+  if (!device_error_word(s0->device)) return fail(QS_ERR_CUDA, "device error word unavailable");
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  BatchCache* bc = (BatchCache*)s0->plan_cache;
+  if (!bc) {
+    bc = new BatchCache();
+    s0->plan_cache = bc;
+  }
+  std::vector<const void*> key;
+  key.reserve(2 * (size_t)count);
+  for (int i = 0; i < count; ++i) {
+    key.push_back(states[i]);
+    key.push_back(circuits[i]);
+  }
+  const bool use_graph = opts && opts->use_graph;
+  const bool hit = use_graph && bc->graph && bc->key == key && bc->dtype == (int)s0->dtype && bc->math == (int)s0->math;
+  if (hit) {
+    QS_CUDA(cudaGraphLaunch(bc->graph, s0->stream));
+    return QS_OK;
+  }
+  if (bc->graph) {
+    cudaGraphExecDestroy(bc->graph);
+    bc->graph = nullptr;
+  }
+  qs_status st = compile_batch<TP>(states, circuits, count, bc);
+  if (st != QS_OK) return st;
+  bc->key = key;
+  bc->dtype = (int)s0->dtype;
+  bc->math = (int)s0->math;
+  // Every state's pending work must finish before the batch touches it.
+  for (int i = 1; i < count; ++i)
+    if (states[i]->stream != s0->stream) QS_CUDA(cudaStreamSynchronize(states[i]->stream));
+  if (!use_graph) return launch_batch<TP>(s0, bc, s0->stream);
+  cudaStream_t cap;
+  QS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    st = launch_batch<TP>(s0, bc, cap);
+    e = cudaStreamEndCapture(cap, &g);
+  }
+  cudaStreamDestroy(cap);
+  if (st != QS_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "batch graph capture");
+  e = cudaGraphInstantiate(&bc->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  QS_CUDA(cudaGraphLaunch(bc->graph, s0->stream));
+  return QS_OK;
+}
+
+}  // namespace
+
+void release_batch_cache(qs_state s) {
+  BatchCache* bc = (BatchCache*)s->plan_cache;
+  if (!bc) return;
+  if (bc->graph) cudaGraphExecDestroy(bc->graph);
+  if (bc->dev) cudaFree(bc->dev);
+  delete bc;
+  s->plan_cache = nullptr;
+}
+
+qs_status batch_run(qs_state* states, const qs_circuit* const* circuits, int count, const qs_run_opts* opts) {
+  if (count < 0 || (count > 0 && (!states || !circuits))) return fail(QS_ERR_ARG, "bad batch");
+  if (count == 0) return QS_OK;
+  const qs_state s0 = states[0];
+  for (int i = 0; i < count; ++i) {
+    if (!states[i] || !circuits[i]) return fail(QS_ERR_ARG, "batch entry %d is NULL", i);
+    if (states[i]->dtype != s0->dtype || states[i]->math != s0->math)
+      return fail(QS_ERR_ARG, "batch entry %d: every state must have the dtype and math mode of the first", i);
+    if (states[i]->device != s0->device) return fail(QS_ERR_ARG, "batch entry %d is on another device", i);
+    const qs_circuit* c = circuits[i];
+    if (c->n_gates < 0 || (c->n_gates > 0 && !c->gates)) return fail(QS_ERR_ARG, "batch circuit %d is malformed", i);
+    for (int64_t g = 0; g < c->n_gates; ++g) {
+      qs_status st = check_gate(states[i], c, g);
+      if (st != QS_OK) return st;
+    }
+  }
+  {
+    std::vector<const void*> seen;
+    for (int i = 0; i < count; ++i) seen.push_back(states[i]->psi);
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+      return fail(QS_ERR_ARG, "a state appears twice in the batch");
+  }
+  if (s0->dtype == QS_C64) return run_batch<TileF32>(states, circuits, count, opts);
+  if (s0->math == QS_MATH_FP64) return run_batch<TileF64>(states, circuits, count, opts);
+  return run_batch<TileDF>(states, circuits, count, opts);
+}
+
+}  // namespace qs

@@ -6,7 +6,12 @@
 
 namespace qs {
 
-void release_plan_cache(qs_state s) { s->plan_cache = nullptr; }
+qs_status run_fused(qs_state s, const qs_circuit* c, int max_high);  // qs_tile.cu
+qs_status batch_run(qs_state* states, const qs_circuit* const* circuits, int count,
+                    const qs_run_opts* opts);  // qs_batch.cu
+void release_batch_cache(qs_state s);           // qs_batch.cu
+
+void release_plan_cache(qs_state s) { release_batch_cache(s); }
 
 // Validates one gate record against the state and returns its control mask.
 qs_status check_gate(const qs_state s, const qs_circuit* c, int64_t gi) {
@@ -28,10 +33,31 @@ qs_status check_gate(const qs_state s, const qs_circuit* c, int64_t gi) {
       if (g.k != 1) return fail(QS_ERR_ARG, "gate %lld: U1 needs k = 1", (long long)gi);
       if (!c->data) return fail(QS_ERR_ARG, "circuit has no data pool");
       break;
-    case QS_GATE_UK:
-      if (g.k > 5) return fail(QS_ERR_ARG, "gate %lld: dense gates take at most 5 targets", (long long)gi);
+    case QS_GATE_UK: {
       if (!c->data) return fail(QS_ERR_ARG, "circuit has no data pool");
+      if (g.k <= 2) break;
+      // Larger matrices are accepted when they are diagonal or permutations.
+      const int dim = 1 << g.k;
+      const double* M = c->data + g.offset;
+      bool diag = true, permlike = true;
+      for (int col = 0; col < dim; ++col) {
+        int ones = 0;
+        for (int r = 0; r < dim; ++r) {
+          const double* z = M + 2 * (r * dim + col);
+          const bool zero = z[0] == 0.0 && z[1] == 0.0;
+          if (r != col && !zero) diag = false;
+          if (z[0] == 1.0 && z[1] == 0.0)
+            ++ones;
+          else if (!zero)
+            permlike = false;
+        }
+        if (ones != 1) permlike = false;
+      }
+      if (!diag && !permlike)
+        return fail(QS_ERR_UNSUPPORTED, "gate %lld: dense matrices on %d targets are not supported (at most 2)",
+                    (long long)gi, g.k);
       break;
+    }
     case QS_GATE_DIAG:
       if (!c->data) return fail(QS_ERR_ARG, "circuit has no data pool");
       break;
@@ -72,13 +98,16 @@ using namespace qs;
 extern "C" {
 
 qs_status qs_fuse_run(qs_state s, const qs_circuit* c, const qs_run_opts* opts) {
-  (void)opts;
   if (!s) return fail(QS_ERR_ARG, "state handle is NULL");
   if (!c || c->n_gates < 0 || (c->n_gates > 0 && !c->gates)) return fail(QS_ERR_ARG, "bad circuit");
+  const int max_fuse = opts ? opts->max_fuse : 0;
+  if (max_fuse < 0 || max_fuse > 6) return fail(QS_ERR_ARG, "max_fuse = %d outside [0, 6]", max_fuse);
   for (int64_t i = 0; i < c->n_gates; ++i) {
     qs_status st = check_gate(s, c, i);
     if (st != QS_OK) return st;
   }
+  if (c->n_gates == 0) return QS_OK;
+  if (max_fuse != 1) return run_fused(s, c, max_fuse == 0 ? 5 : max_fuse);
   for (int64_t i = 0; i < c->n_gates; ++i) {
     qs_status st = apply_gate_record(s, c, c->gates[i]);
     if (st != QS_OK) return st;
@@ -87,12 +116,7 @@ qs_status qs_fuse_run(qs_state s, const qs_circuit* c, const qs_run_opts* opts) 
 }
 
 qs_status qs_batch_run(qs_state* states, const qs_circuit* const* circuits, int count, const qs_run_opts* opts) {
-  if (count < 0 || (count > 0 && (!states || !circuits))) return fail(QS_ERR_ARG, "bad batch");
-  for (int i = 0; i < count; ++i) {
-    qs_status st = qs_fuse_run(states[i], circuits[i], opts);
-    if (st != QS_OK) return st;
-  }
-  return QS_OK;
+  return batch_run(states, circuits, count, opts);
 }
 
 }  // extern "C"

@@ -1,0 +1,401 @@
+// Host-side fuser: turns a gate list into fused blocks of tile ops.
+//
+// A block is a set of gates applied in one pass over the state: their targets
+// must be tile qubits (the low qubits plus at most max_high "high" qubits,
+// see qs_tile.cuh); diagonal gates need no tile qubits.  Blocks are grown
+// greedily over a window of the remaining gates: a gate that cannot join
+// blocks the qubits it touches for every later gate, so later gates only move
+// ahead of gates they commute with (disjoint qubits).  Used by the per-circuit
+// runner (qs_tile.cu) and by the batched kernel (qs_batch.cu).
+#pragma once
+#include <algorithm>
+#include <cstring>
+#include <functional>
+#include <vector>
+
+#include "qs_internal.h"
+#include "qs_tile.cuh"
+
+namespace qs {
+namespace fuser {
+
+inline bool is_c(const double* z, double re, double im) { return z[0] == re && z[1] == im; }
+
+// One gate record in normalised form.
+struct FGate {
+  int kind;  // QS_GATE_*
+  int k;
+  int targets[QS_MAX_TARGETS];
+  uint64_t ctrl;
+  const double* data;
+  const uint32_t* perm;
+  bool diagonal;        // needs no tile qubits
+  uint64_t qubit_mask;  // targets | controls
+  uint64_t tmask;       // targets that must be tile qubits
+};
+
+inline bool matrix_is_diag(const double* M, int dim) {
+  for (int r = 0; r < dim; ++r)
+    for (int c = 0; c < dim; ++c)
+      if (r != c && !is_c(M + 2 * (r * dim + c), 0, 0)) return false;
+  return true;
+}
+
+inline FGate normalise(const qs_circuit* c, const qs_gate& g) {
+  FGate f;
+  std::memset(&f, 0, sizeof(f));
+  f.kind = g.kind;
+  f.k = g.k;
+  for (int j = 0; j < g.k; ++j) f.targets[j] = g.targets[j];
+  f.ctrl = g.ctrl_mask;
+  if (g.kind == QS_GATE_PERM)
+    f.perm = c->perm + g.offset;
+  else
+    f.data = c->data + g.offset;
+  uint64_t tm = 0;
+  for (int j = 0; j < g.k; ++j) tm |= 1ull << g.targets[j];
+  f.qubit_mask = tm | g.ctrl_mask;
+  if (g.kind == QS_GATE_DIAG)
+    f.diagonal = true;
+  else if (g.kind == QS_GATE_U1 || g.kind == QS_GATE_UK)
+    f.diagonal = matrix_is_diag(f.data, 1 << g.k);
+  f.tmask = f.diagonal ? 0 : tm;
+  return f;
+}
+
+// Gates a tile op can express: dense matrices on at most 2 targets,
+// diagonals and permutations on at most 8.
+inline bool tileable(const FGate& g) {
+  if (g.kind == QS_GATE_DIAG || g.kind == QS_GATE_PERM || g.diagonal) return g.k <= 8;
+  return g.k <= 2;
+}
+
+struct Geom {
+  int L = 0, m = 0;
+  int hq[kTileMaxHigh] = {0};
+};
+
+// Smallest tile geometry whose tile qubits include `need`: L = tile_log - m
+// low qubits and the needed qubits at or above L as high qubits (m of them).
+inline bool geometry(uint64_t need, int n, int tile_log, int max_high, int min_chunk_log, Geom* g) {
+  if (n <= tile_log) {
+    g->L = n;
+    g->m = 0;
+    return true;
+  }
+  for (int m = 0; m <= max_high && m <= kTileMaxHigh; ++m) {
+    const int L = tile_log - m;
+    if (L < min_chunk_log) return false;
+    int cnt = 0;
+    for (int q = L; q < n; ++q)
+      if ((need >> q) & 1ull) {
+        if (cnt < kTileMaxHigh) g->hq[cnt] = q;
+        ++cnt;
+      }
+    if (cnt <= m) {  // the smallest feasible m has cnt == m
+      g->L = L;
+      g->m = cnt;
+      return true;
+    }
+  }
+  return false;
+}
+
+struct Limits {
+  int ops, coefs, perm_bytes;
+};
+
+template <class Coef>
+struct BlockOut {
+  Geom geom;
+  std::vector<TileOp> ops;
+  std::vector<Coef> coefs;
+  std::vector<uint8_t> perm;
+};
+
+// Translates gates into tile ops for one block geometry.
+template <class P>
+struct PlanBuilder {
+  using Coef = typename P::Coef;
+  BlockOut<Coef>* out;
+  Limits lim;
+  int local_of[64];
+
+  PlanBuilder(BlockOut<Coef>* o, const Geom& g, Limits l) : out(o), lim(l) {
+    out->geom = g;
+    out->ops.clear();
+    out->coefs.clear();
+    out->perm.clear();
+    for (int q = 0; q < 64; ++q) local_of[q] = -1;
+    for (int q = 0; q < g.L; ++q) local_of[q] = q;
+    for (int j = 0; j < g.m; ++j) local_of[g.hq[j]] = g.L + j;
+  }
+
+  bool room(int ops, int coefs, int perm_bytes) const {
+    return (int)out->ops.size() + ops <= lim.ops && (int)out->coefs.size() + coefs <= lim.coefs &&
+           (int)out->perm.size() + perm_bytes <= lim.perm_bytes;
+  }
+
+  static TileOp blank() {
+    TileOp op;
+    std::memset(&op, 0, sizeof(op));
+    return op;
+  }
+
+  // Local controls are inserted as fixed 1s; controls on free qubits become
+  // the op's tile predicate.
+  void controls(TileOp& op, uint64_t ctrl, std::vector<int>& ins, uint32_t& fixed) const {
+    for (int q = 0; q < 64; ++q) {
+      if (!((ctrl >> q) & 1ull)) continue;
+      if (local_of[q] >= 0) {
+        ins.push_back(local_of[q]);
+        fixed |= 1u << local_of[q];
+      } else {
+        op.gmask |= 1ull << q;
+        op.gpat |= 1ull << q;
+      }
+    }
+  }
+
+  static bool set_positions(TileOp& op, std::vector<int> ins, uint32_t fixed) {
+    if ((int)ins.size() > kTileMaxPos) return false;
+    std::sort(ins.begin(), ins.end());
+    op.npos = (uint8_t)ins.size();
+    for (size_t j = 0; j < ins.size(); ++j) op.himask[j] = ~((1u << ins[j]) - 1u);
+    op.ifixed = fixed;
+    return true;
+  }
+
+  uint16_t add_coefs(const double* z, int count) {
+    const uint16_t at = (uint16_t)out->coefs.size();
+    for (int j = 0; j < count; ++j) out->coefs.push_back(P::make_coef(z[2 * j], z[2 * j + 1]));
+    return at;
+  }
+
+  bool phase(uint64_t mask, uint64_t pattern, const double* c) {
+    if (!room(1, 1, 0)) return false;
+    TileOp op = blank();
+    std::vector<int> ins;
+    uint32_t fixed = 0;
+    for (int q = 0; q < 64; ++q) {
+      if (!((mask >> q) & 1ull)) continue;
+      const bool one = (pattern >> q) & 1ull;
+      if (local_of[q] >= 0) {
+        ins.push_back(local_of[q]);
+        if (one) fixed |= 1u << local_of[q];
+      } else {
+        op.gmask |= 1ull << q;
+        if (one) op.gpat |= 1ull << q;
+      }
+    }
+    if (!set_positions(op, ins, fixed)) return false;
+    if (is_c(c, -1, 0)) {
+      op.kind = TOP_NEG;
+    } else {
+      op.kind = TOP_PHASE;
+      op.coef = add_coefs(c, 1);
+    }
+    out->ops.push_back(op);
+    return true;
+  }
+
+  bool diag(const int* targets, int k, uint64_t ctrl, const double* d) {
+    int n_other = 0, v_other = -1;
+    for (int v = 0; v < (1 << k); ++v)
+      if (!is_c(d + 2 * v, 1, 0)) {
+        ++n_other;
+        v_other = v;
+      }
+    if (n_other == 0) return true;
+    if (n_other == 1) {
+      uint64_t mask = ctrl, pattern = ctrl;
+      for (int j = 0; j < k; ++j) {
+        mask |= 1ull << targets[j];
+        if ((v_other >> j) & 1) pattern |= 1ull << targets[j];
+      }
+      return phase(mask, pattern, d + 2 * v_other);
+    }
+    if (!room(1, 1 << k, 0)) return false;
+    TileOp op = blank();
+    op.kind = TOP_DIAG;
+    op.k = (uint8_t)k;
+    std::vector<int> ins;
+    uint32_t fixed = 0;
+    controls(op, ctrl, ins, fixed);
+    if (!set_positions(op, ins, fixed)) return false;
+    int nl = 0;
+    for (int j = 0; j < k; ++j) {
+      const int lq = local_of[targets[j]];
+      if (lq >= 0) {
+        op.tpos[nl] = (uint8_t)lq;
+        op.tj[nl] = (uint8_t)j;
+        ++nl;
+        op.gq[j] = 0xFF;
+      } else {
+        op.gq[j] = (uint8_t)targets[j];
+      }
+    }
+    op.nloc = (uint8_t)nl;
+    op.coef = add_coefs(d, 1 << k);
+    out->ops.push_back(op);
+    return true;
+  }
+
+  bool pairs(uint8_t kind, int t, uint64_t ctrl, const double* U) {
+    if (!room(1, U ? 4 : 0, 0)) return false;
+    TileOp op = blank();
+    op.kind = kind;
+    op.tpos[0] = (uint8_t)local_of[t];
+    std::vector<int> ins{local_of[t]};
+    uint32_t fixed = 0;
+    controls(op, ctrl, ins, fixed);
+    if (!set_positions(op, ins, fixed)) return false;
+    if (U) op.coef = add_coefs(U, 4);
+    out->ops.push_back(op);
+    return true;
+  }
+
+  bool dense2(int t0, int t1, uint64_t ctrl, const double* U) {
+    if (!room(1, 16, 0)) return false;
+    TileOp op = blank();
+    op.kind = TOP_DENSE2;
+    op.tpos[0] = (uint8_t)local_of[t0];
+    op.tpos[1] = (uint8_t)local_of[t1];
+    std::vector<int> ins{local_of[t0], local_of[t1]};
+    uint32_t fixed = 0;
+    controls(op, ctrl, ins, fixed);
+    if (!set_positions(op, ins, fixed)) return false;
+    op.coef = add_coefs(U, 16);
+    out->ops.push_back(op);
+    return true;
+  }
+
+  bool perm(const int* targets, int k, uint64_t ctrl, const uint32_t* p) {
+    if (k > 8 || !room(1, 0, 1 << k)) return false;
+    TileOp op = blank();
+    op.kind = TOP_PERM;
+    op.k = (uint8_t)k;
+    for (int j = 0; j < k; ++j) op.tpos[j] = (uint8_t)local_of[targets[j]];
+    for (int q = 0; q < 64; ++q) {
+      if (!((ctrl >> q) & 1ull)) continue;
+      if (local_of[q] >= 0) {
+        op.lmask |= 1u << local_of[q];
+      } else {
+        op.gmask |= 1ull << q;
+        op.gpat |= 1ull << q;
+      }
+    }
+    op.ptab = (uint16_t)out->perm.size();
+    const size_t at = out->perm.size();
+    out->perm.resize(at + (1u << k));
+    for (int v = 0; v < (1 << k); ++v) out->perm[at + p[v]] = (uint8_t)v;  // inverse table
+    out->ops.push_back(op);
+    return true;
+  }
+
+  // Translate one gate; false if the block has no room for it.
+  bool add(const FGate& g) {
+    if (g.kind == QS_GATE_DIAG) return diag(g.targets, g.k, g.ctrl, g.data);
+    if (g.kind == QS_GATE_PERM) {
+      bool ident = true;
+      for (int v = 0; v < (1 << g.k); ++v) ident = ident && g.perm[v] == (uint32_t)v;
+      if (ident) return true;
+      if (g.k == 1) return pairs(TOP_XSWAP, g.targets[0], g.ctrl, nullptr);
+      return perm(g.targets, g.k, g.ctrl, g.perm);
+    }
+    const int dim = 1 << g.k;
+    if (g.diagonal) {
+      std::vector<double> d(2 * dim);
+      for (int v = 0; v < dim; ++v) {
+        d[2 * v] = g.data[2 * (v * dim + v)];
+        d[2 * v + 1] = g.data[2 * (v * dim + v) + 1];
+      }
+      return diag(g.targets, g.k, g.ctrl, d.data());
+    }
+    if (g.k == 1) {
+      const double* U = g.data;
+      if (is_c(U, 0, 0) && is_c(U + 6, 0, 0)) {
+        if (is_c(U + 2, 1, 0) && is_c(U + 4, 1, 0)) return pairs(TOP_XSWAP, g.targets[0], g.ctrl, nullptr);
+        if (is_c(U + 2, 0, -1) && is_c(U + 4, 0, 1)) return pairs(TOP_Y, g.targets[0], g.ctrl, nullptr);
+      }
+      return pairs(TOP_DENSE1, g.targets[0], g.ctrl, U);
+    }
+    if (g.k == 2) {
+      // Permutation matrices given densely become table permutations.
+      bool permlike = true;
+      uint32_t p[4] = {0, 0, 0, 0};
+      for (int c = 0; c < 4 && permlike; ++c) {
+        int ones = 0;
+        for (int r = 0; r < 4; ++r) {
+          const double* z = g.data + 2 * (r * 4 + c);
+          if (is_c(z, 1, 0)) {
+            ++ones;
+            p[c] = (uint32_t)r;
+          } else if (!is_c(z, 0, 0)) {
+            permlike = false;
+          }
+        }
+        if (ones != 1) permlike = false;
+      }
+      if (permlike) return perm(g.targets, 2, g.ctrl, p);
+      return dense2(g.targets[0], g.targets[1], g.ctrl, g.data);
+    }
+    return false;
+  }
+};
+
+// Estimated pool use of one gate.
+inline void pool_need(const FGate& g, int* coefs, int* perm_bytes) {
+  *coefs = 0;
+  *perm_bytes = 0;
+  if (g.kind == QS_GATE_PERM)
+    *perm_bytes = 1 << g.k;
+  else if (g.kind == QS_GATE_DIAG || g.diagonal)
+    *coefs = 1 << g.k;
+  else if (g.k == 2)
+    *coefs = 16;  // or a 4-entry permutation table
+  else
+    *coefs = 4;
+  if (g.k == 2 && !g.diagonal && g.kind == QS_GATE_UK) *perm_bytes = 4;
+}
+
+// Choose the next block starting at the first untaken gate.  Returns the
+// member indices (in application order) and the geometry; an empty result
+// means gate `next` cannot be placed in a tile with these limits.
+inline std::vector<size_t> choose_block(const std::vector<FGate>& gates, const std::vector<char>& taken, size_t next,
+                                        int n, int tile_log, int max_high, int min_chunk_log, Limits lim,
+                                        size_t window, Geom* geom_out) {
+  std::vector<size_t> members;
+  const FGate& g0 = gates[next];
+  Geom geom;
+  if (!tileable(g0) || !geometry(g0.tmask, n, tile_log, max_high, min_chunk_log, &geom)) return members;
+  uint64_t need = 0, blocked = 0;
+  const uint64_t all = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+  int ops = 0, coefs = 0, pbytes = 0;
+  for (size_t i = next; i < gates.size() && i < next + window; ++i) {
+    if (taken[i]) continue;
+    const FGate& g = gates[i];
+    bool ok = tileable(g) && !(g.qubit_mask & blocked);
+    Geom trial;
+    int c_need = 0, p_need = 0;
+    pool_need(g, &c_need, &p_need);
+    if (ok) ok = geometry(need | g.tmask, n, tile_log, max_high, min_chunk_log, &trial);
+    if (ok && (ops + 1 > lim.ops || coefs + c_need > lim.coefs || pbytes + p_need > lim.perm_bytes)) ok = false;
+    if (ok) {
+      members.push_back(i);
+      need |= g.tmask;
+      geom = trial;
+      ++ops;
+      coefs += c_need;
+      pbytes += p_need;
+    } else {
+      blocked |= g.qubit_mask;
+      if (blocked == all) break;
+    }
+  }
+  *geom_out = geom;
+  return members;
+}
+
+}  // namespace fuser
+}  // namespace qs

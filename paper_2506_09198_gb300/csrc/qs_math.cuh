@@ -62,35 +62,6 @@ __device__ __forceinline__ void d2ff(double x, float& h, float& l) {
 }
 
 // ---------------------------------------------------------------------------
-// Float-float dot-product accumulator: sum of (ah+al)(xh+xl) terms.
-// ---------------------------------------------------------------------------
-struct DFAcc {
-  float s;  // sum of the exact product heads, kept exact through TwoSum
-  float c;  // all lower-order parts
-};
-
-__device__ __forceinline__ void df_first(DFAcc& a, float ah, float al, float xh, float xl) {
-  const float p = ah * xh;
-  const float e = __fmaf_rn(ah, xh, -p);  // p + e = ah * xh exactly
-  a.s = p;
-  a.c = __fmaf_rn(al, xh, __fmaf_rn(ah, xl, e));
-}
-
-__device__ __forceinline__ void df_add(DFAcc& a, float ah, float al, float xh, float xl) {
-  const float p = ah * xh;
-  const float e = __fmaf_rn(ah, xh, -p);
-  const float s = a.s + p;  // TwoSum(a.s, p): s + err = a.s + p exactly
-  const float bb = s - a.s;
-  const float err = (a.s - (s - bb)) + (p - bb);
-  a.s = s;
-  a.c = __fmaf_rn(al, xh, __fmaf_rn(ah, xl, a.c + (err + e)));
-}
-
-__device__ __forceinline__ double df_round(const DFAcc& a) {
-  return f2d_exact(a.s) + f2d_exact(a.c);
-}
-
-// ---------------------------------------------------------------------------
 // Policies.  Each provides:
 //   Amp       storage type of one amplitude
 //   Val       working value of one amplitude
@@ -100,29 +71,6 @@ __device__ __forceinline__ double df_round(const DFAcc& a) {
 //   mac_round<K>(coefs, vals) -> Amp   sum_k coefs[k] * vals[k], rounded to
 //                                      the storage type
 // ---------------------------------------------------------------------------
-struct MathF32 {
-  using Amp = float2;
-  struct Val { float re, im; };
-  struct Coef { float re, im; };
-  static __host__ Coef make_coef(double re, double im) { return Coef{(float)re, (float)im}; }
-  static __device__ __forceinline__ Val load(const Amp& a) { return Val{a.x, a.y}; }
-  static __device__ __forceinline__ Amp pack(const Val& v) { return make_float2(v.re, v.im); }
-  template <int K>
-  static __device__ __forceinline__ Val mac(const Coef* m, const Val* v) {
-    float re = 0.f, im = 0.f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      re = __fmaf_rn(m[k].re, v[k].re, re);
-      re = __fmaf_rn(-m[k].im, v[k].im, re);
-      im = __fmaf_rn(m[k].re, v[k].im, im);
-      im = __fmaf_rn(m[k].im, v[k].re, im);
-    }
-    return Val{re, im};
-  }
-  template <int K>
-  static __device__ __forceinline__ Amp mac_round(const Coef* m, const Val* v) { return pack(mac<K>(m, v)); }
-};
-
 struct MathF64 {
   using Amp = double2;
   struct Val { double re, im; };
@@ -204,6 +152,34 @@ struct DF2Acc {
     C = fma2(a.h, xl, C);
     C = fma2(a.l, xh, C);
     S = s;
+  }
+};
+
+// complex64 with packed FP32x2 multiply-adds: (re, im) += (mr, mr)(vr, vi)
+// + (-mi, mi)(vi, vr), two instructions per complex multiply-add.
+struct MathF32 {
+  using Amp = float2;
+  struct Val {
+    float2 v, vs;  // (re, im) and (im, re)
+  };
+  struct Coef {
+    float2 a, b;   // (mr, mr) and (-mi, mi)
+  };
+  static __host__ Coef make_coef(double re, double im) {
+    const float r = (float)re, i = (float)im;
+    return Coef{make_float2(r, r), make_float2(-i, i)};
+  }
+  static __device__ __forceinline__ Val load(const Amp& a) { return Val{a, make_float2(a.y, a.x)}; }
+  template <int K>
+  static __device__ __forceinline__ Amp mac_round(const Coef* m, const Val* v) {
+    float2 acc = mul2(m[0].a, v[0].v);
+    acc = fma2(m[0].b, v[0].vs, acc);
+#pragma unroll
+    for (int k = 1; k < K; ++k) {
+      acc = fma2(m[k].a, v[k].v, acc);
+      acc = fma2(m[k].b, v[k].vs, acc);
+    }
+    return acc;
   }
 };
 

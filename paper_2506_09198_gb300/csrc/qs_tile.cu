@@ -1,0 +1,279 @@
+// Fused-block kernel and host fuser.
+//
+// k_tile is persistent (one or two CTAs per SM).  A producer warp streams
+// tiles between HBM and shared memory with bulk asynchronous copies
+// (cp.async.bulk, the TMA engine) — one copy per contiguous chunk, completion
+// tracked by mbarrier transaction counts — through a ring of kStages buffers.
+// Eight consumer warps apply the block's gates to the tile in shared memory,
+// one gate after another, and hand the buffer back; the producer writes it to
+// HBM with bulk stores and refills it.  Loads, arithmetic and stores of
+// different tiles overlap, and the state is read and written once per block
+// however many gates the block holds (gate fusion / cache blocking, Sec. I).
+//
+// Complex128 tiles are converted once on arrival to float-float form (head
+// and tail FP32 pairs, same 16 bytes) so every gate of the block runs on the
+// FP32 pipes without re-splitting doubles; they are rounded back to IEEE
+// double once before the store.
+//
+// Every wait is bounded (about 2 s of %globaltimer): on expiry the kernel
+// records QS_ERR_TIMEOUT's code in the device error word, all warps agree to
+// stop, the producer waits for the copies it issued, and the kernel returns.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "qs_internal.h"
+#include "qs_math.cuh"
+#include "qs_tile.cuh"
+#include "qs_tile_dev.cuh"
+#include "qs_fuser.h"
+
+namespace qs {
+
+template <class TP>
+__global__ void __launch_bounds__(kTileThreads, 2) k_tile(typename TP::Glob* __restrict__ psi,
+                                                       const __grid_constant__ TilePlan<typename TP::M::Coef> plan,
+                                                       uint32_t* __restrict__ err) {
+  using Glob = typename TP::Glob;
+  using Sm = typename TP::Sm;
+  static_assert(sizeof(Glob) == sizeof(Sm), "in-place tile conversion");
+  extern __shared__ __align__(128) unsigned char smem[];
+  const uint32_t tile_amps = 1u << (plan.L + plan.m);
+  const uint32_t tile_bytes = tile_amps * (uint32_t)sizeof(Glob);
+  const uint32_t chunk_amps = 1u << plan.L;
+  const uint32_t chunk_bytes = chunk_amps * (uint32_t)sizeof(Glob);
+  const uint32_t n_chunks = 1u << plan.m;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * tile_bytes);
+  uint64_t* done = full + kStages;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&done[s], kTileConsumers);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  if (tid >= kTileConsumers) {
+    // ---------------- producer ----------------
+    if (tid != kTileConsumers) return;
+    uint32_t j = 0;
+    bool ok = true;
+    uint32_t loads_issued = 0;
+    for (;; ++j) {
+      const uint64_t tau = blockIdx.x + (uint64_t)j * gridDim.x;
+      if (tau >= plan.n_tiles) break;
+      const int s = (int)(j % kStages);
+      unsigned char* buf = smem + (size_t)s * tile_bytes;
+      if (j >= (uint32_t)kStages) {
+        const uint32_t jp = j - kStages;
+        if (!mbar_wait(&done[s], (jp / kStages) & 1u, err)) {
+          ok = false;
+          break;
+        }
+        const uint64_t bprev = tile_base(blockIdx.x + (uint64_t)jp * gridDim.x, plan.L, plan.m, plan.base_high);
+        for (uint32_t c = 0; c < n_chunks; ++c)
+          bulk_store(psi + bprev + plan.chunk_off[c], buf + (size_t)c * chunk_bytes, chunk_bytes);
+        bulk_commit();
+        bulk_wait_read_all();
+      }
+      const uint64_t b = tile_base(tau, plan.L, plan.m, plan.base_high);
+      mbar_expect_tx(&full[s], tile_bytes);
+      for (uint32_t c = 0; c < n_chunks; ++c)
+        bulk_load(buf + (size_t)c * chunk_bytes, psi + b + plan.chunk_off[c], chunk_bytes, &full[s]);
+      ++loads_issued;
+    }
+    const uint32_t count = j;  // tiles whose loads were issued
+    if (ok) {
+      const uint32_t first = count > (uint32_t)kStages ? count - kStages : 0u;
+      for (uint32_t jj = first; jj < count; ++jj) {
+        const int s = (int)(jj % kStages);
+        if (!mbar_wait(&done[s], (jj / kStages) & 1u, err)) {
+          ok = false;
+          break;
+        }
+        const uint64_t b = tile_base(blockIdx.x + (uint64_t)jj * gridDim.x, plan.L, plan.m, plan.base_high);
+        unsigned char* buf = smem + (size_t)s * tile_bytes;
+        for (uint32_t c = 0; c < n_chunks; ++c)
+          bulk_store(psi + b + plan.chunk_off[c], buf + (size_t)c * chunk_bytes, chunk_bytes);
+        bulk_commit();
+      }
+    }
+    if (!ok) {
+      // Let every load this CTA issued land before the CTA's shared memory
+      // goes away (bounded; the copies are plain in-range reads).
+      const uint32_t first = loads_issued > (uint32_t)kStages ? loads_issued - kStages : 0u;
+      for (uint32_t jj = first; jj < loads_issued; ++jj) {
+        const int s = (int)(jj % kStages);
+        const uint64_t t0 = global_ns();
+        while (!mbar_try(&full[s], (jj / kStages) & 1u) && global_ns() - t0 < kWaitNs) {
+        }
+      }
+    }
+    bulk_wait_all();
+    return;
+  }
+
+  // ---------------- consumers ----------------
+  for (uint32_t j = 0;; ++j) {
+    const uint64_t tau = blockIdx.x + (uint64_t)j * gridDim.x;
+    if (tau >= plan.n_tiles) break;
+    const int s = (int)(j % kStages);
+    const bool ok = mbar_wait(&full[s], (j / kStages) & 1u, err);
+    if (consumers_any(!ok)) break;
+    Sm* t = reinterpret_cast<Sm*>(smem + (size_t)s * tile_bytes);
+    if constexpr (!std::is_same<Glob, Sm>::value) {
+      for (uint32_t e = tid; e < tile_amps; e += kTileConsumers) t[e] = TP::to_sm(reinterpret_cast<Glob*>(t)[e]);
+      consumers_sync();
+    }
+    const uint64_t base = tile_base(tau, plan.L, plan.m, plan.base_high);
+    for (int o = 0; o < plan.nops; ++o) {
+      const TileOp& op = plan.ops[o];
+      if ((base & op.gmask) != op.gpat) continue;
+      apply_op<TP>(t, op, plan.coefs, plan.perm, tile_amps, base, tid);
+      consumers_sync();
+    }
+    if constexpr (!std::is_same<Glob, Sm>::value) {
+      for (uint32_t e = tid; e < tile_amps; e += kTileConsumers) reinterpret_cast<Glob*>(t)[e] = TP::from_sm(t[e]);
+    }
+    fence_async_smem();
+    mbar_arrive(&done[s]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host: blocks -> plans -> launches
+// ---------------------------------------------------------------------------
+namespace {
+
+using namespace fuser;
+
+constexpr int kMinChunkLog128 = 3;  // chunks of at least 128 bytes
+constexpr int kMinChunkLog64 = 4;
+
+template <class Coef>
+void fill_plan(TilePlan<Coef>* plan, int n, const BlockOut<Coef>& bo) {
+  const Geom& g = bo.geom;
+  std::memset(plan, 0, sizeof(*plan));
+  plan->n = n;
+  plan->L = g.L;
+  plan->m = g.m;
+  plan->n_tiles = 1ull << (n - g.L - g.m);
+  for (int j = 0; j < g.m; ++j) plan->base_high[j] = ~((1ull << g.hq[j]) - 1ull);
+  for (int c = 0; c < (1 << g.m); ++c) {
+    uint64_t off = 0;
+    for (int j = 0; j < g.m; ++j)
+      if ((c >> j) & 1) off |= 1ull << g.hq[j];
+    plan->chunk_off[c] = off;
+  }
+  plan->nops = (int)bo.ops.size();
+  std::memcpy(plan->ops, bo.ops.data(), bo.ops.size() * sizeof(TileOp));
+  std::memcpy(plan->coefs, bo.coefs.data(), bo.coefs.size() * sizeof(Coef));
+  if (!bo.perm.empty()) std::memcpy(plan->perm, bo.perm.data(), bo.perm.size());
+}
+
+template <class TP>
+qs_status launch_plan(qs_state s, const TilePlan<typename TP::M::Coef>& plan) {
+  const size_t tile_bytes = sizeof(typename TP::Glob) << (plan.L + plan.m);
+  const size_t smem = kStages * tile_bytes + 2 * kStages * sizeof(uint64_t);
+  auto kern = k_tile<TP>;
+  static std::mutex mu;
+  static std::unordered_map<int, int> occ_cache;
+  int occ = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    const int key = (int)smem;
+    auto it = occ_cache.find(key);
+    if (it == occ_cache.end()) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_tile)");
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTileThreads, smem) != cudaSuccess || occ < 1)
+        occ = 1;
+      occ_cache[key] = occ;
+    } else {
+      occ = it->second;
+    }
+  }
+  const uint64_t full = (uint64_t)sm_count(s->device) * occ;
+  const unsigned grid = (unsigned)(plan.n_tiles < full ? plan.n_tiles : full);
+  uint32_t* err = device_error_word(s->device);
+  if (!err) return fail(QS_ERR_CUDA, "device error word unavailable");
+  kern<<<grid, kTileThreads, smem, s->stream>>>((typename TP::Glob*)s->psi, plan, err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "k_tile");
+  return QS_OK;
+}
+
+qs_status dispatch_single(qs_state s, const FGate& g) {
+  if (g.kind == QS_GATE_PERM) return dispatch_perm(s, g.targets, g.k, g.ctrl, g.perm);
+  if (g.kind == QS_GATE_DIAG) return dispatch_diag(s, g.targets, g.k, g.ctrl, g.data);
+  if (g.kind == QS_GATE_U1) return dispatch_u1(s, g.targets[0], g.ctrl, g.data);
+  return dispatch_uk(s, g.targets, g.k, g.ctrl, g.data);
+}
+
+template <class TP>
+qs_status run_blocks(qs_state s, const std::vector<FGate>& gates, int max_high) {
+  using Coef = typename TP::M::Coef;
+  const int n = s->n;
+  const int min_chunk = sizeof(typename TP::Glob) == 16 ? kMinChunkLog128 : kMinChunkLog64;
+  const Limits lim{kTileMaxOps, kTileMaxCoefs, kTileMaxPermBytes};
+  static thread_local std::vector<unsigned char> plan_mem;
+  plan_mem.resize(sizeof(TilePlan<Coef>));
+  TilePlan<Coef>* plan = reinterpret_cast<TilePlan<Coef>*>(plan_mem.data());
+  BlockOut<Coef> bo;
+  std::vector<char> taken(gates.size(), 0);
+  size_t next = 0;
+  while (next < gates.size()) {
+    if (taken[next]) {
+      ++next;
+      continue;
+    }
+    Geom geom;
+    const std::vector<size_t> members =
+        choose_block(gates, taken, next, n, TP::kTileLog, max_high, min_chunk, lim, 512, &geom);
+    // A gate that fits no tile, or a block of one gate (staging gains
+    // nothing), runs on the per-gate kernels.
+    if (members.size() <= 1) {
+      qs_status st = dispatch_single(s, gates[next]);
+      if (st != QS_OK) return st;
+      taken[next] = 1;
+      continue;
+    }
+    PlanBuilder<typename TP::M> pb(&bo, geom, lim);
+    size_t emitted = 0;
+    for (size_t idx : members) {
+      if (!pb.add(gates[idx])) break;
+      taken[idx] = 1;
+      ++emitted;
+    }
+    if (emitted == 0) {
+      qs_status st = dispatch_single(s, gates[next]);
+      if (st != QS_OK) return st;
+      taken[next] = 1;
+      continue;
+    }
+    if (!bo.ops.empty()) {
+      fill_plan(plan, n, bo);
+      qs_status st = launch_plan<TP>(s, *plan);
+      if (st != QS_OK) return st;
+    }
+  }
+  return QS_OK;
+}
+
+}  // namespace
+
+qs_status run_fused(qs_state s, const qs_circuit* c, int max_high) {
+  std::vector<FGate> gates;
+  gates.reserve((size_t)c->n_gates);
+  for (int64_t i = 0; i < c->n_gates; ++i) gates.push_back(normalise(c, c->gates[i]));
+  if (max_high > kTileMaxHigh) max_high = kTileMaxHigh;
+  if (s->dtype == QS_C64) return run_blocks<TileF32>(s, gates, max_high);
+  if (s->math == QS_MATH_FP64) return run_blocks<TileF64>(s, gates, max_high);
+  return run_blocks<TileDF>(s, gates, max_high);
+}
+
+}  // namespace qs
