@@ -15,6 +15,7 @@
 // memory; eight consumer warps apply the ops.  Waits are bounded as in k_tile.
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <numeric>
 #include <vector>
@@ -226,6 +227,9 @@ struct BatchCache {
 };
 
 std::mutex g_batch_mu;
+// One compiled-batch workspace per (device, stream): reuse is ordered by the
+// stream, so no launch can see a workspace that a later call overwrites.
+std::map<std::pair<int, cudaStream_t>, BatchCache*> g_batch_caches;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -326,7 +330,8 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
   std::memcpy(host.data() + bc->off_ops, ops.data(), ops.size() * sizeof(TileOp));
   std::memcpy(host.data() + bc->off_coefs, coefs.data(), coefs.size() * sizeof(Coef));
   if (!perm.empty()) std::memcpy(host.data() + bc->off_perm, perm.data(), perm.size());
-  QS_CUDA(cudaMemcpy(bc->dev, host.data(), off, cudaMemcpyHostToDevice));
+  // Stream-ordered after the previous batch that used this buffer.
+  QS_CUDA(cudaMemcpyAsync(bc->dev, host.data(), off, cudaMemcpyHostToDevice, states[0]->stream));
   bc->n_states = (uint32_t)count;
   return QS_OK;
 }
@@ -363,11 +368,9 @@ qs_status run_batch(qs_state* states, const qs_circuit* const* circuits, int cou
   qs_state s0 = states[0];
   if (!device_error_word(s0->device)) return fail(QS_ERR_CUDA, "device error word unavailable");
   std::lock_guard<std::mutex> lk(g_batch_mu);
-  BatchCache* bc = (BatchCache*)s0->plan_cache;
-  if (!bc) {
-    bc = new BatchCache();
-    s0->plan_cache = bc;
-  }
+  BatchCache*& slot = g_batch_caches[std::make_pair(s0->device, s0->stream)];
+  if (!slot) slot = new BatchCache();
+  BatchCache* bc = slot;
   std::vector<const void*> key;
   key.reserve(2 * (size_t)count);
   for (int i = 0; i < count; ++i) {
@@ -413,14 +416,7 @@ qs_status run_batch(qs_state* states, const qs_circuit* const* circuits, int cou
 
 }  // namespace
 
-void release_batch_cache(qs_state s) {
-  BatchCache* bc = (BatchCache*)s->plan_cache;
-  if (!bc) return;
-  if (bc->graph) cudaGraphExecDestroy(bc->graph);
-  if (bc->dev) cudaFree(bc->dev);
-  delete bc;
-  s->plan_cache = nullptr;
-}
+void release_batch_cache(qs_state s) { (void)s; }
 
 qs_status batch_run(qs_state* states, const qs_circuit* const* circuits, int count, const qs_run_opts* opts) {
   if (count < 0 || (count > 0 && (!states || !circuits))) return fail(QS_ERR_ARG, "bad batch");

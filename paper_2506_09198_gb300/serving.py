@@ -1,0 +1,264 @@
+"""Continuous-batching serving loop over the libqs C ABI.
+
+Requests (a circuit on n qubits) arrive over time.  The server admits a
+waiting request when its state fits the HBM budget (2^n amplitudes x 8 or 16
+bytes) and a slot is free, keeps admitted states resident on the device, and
+every scheduler tick advances every resident circuit by its next chunk of
+gates ("layer"):
+  - states of at most ``small_n`` qubits: one ``qs_batch_run`` launch carries
+    the next chunk of all of them;
+  - larger states: ``qs_fuse_run`` of their next chunk on their own stream.
+New arrivals join at the next tick, so their work overlaps on the device with
+the requests already running.  When a circuit's last chunk is done the server
+reads its result (marginal probabilities of the lowest ``result_qubits``
+qubits and the norm), frees the state and records the latency (arrival to
+result).
+
+Chunk boundaries and fusion depend only on the request's own gates, so a
+request's result does not depend on what else is in flight.
+
+All compute runs in libqs kernels; this module only schedules.
+"""
+from __future__ import annotations
+
+import heapq
+import math
+import time
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional
+
+import numpy as np
+
+from . import qs
+
+
+@dataclass
+class Request:
+    rid: int
+    n: int
+    gates: list
+    arrival: float = 0.0          # seconds on the server clock
+    kind: str = ""
+    result_qubits: int = 8
+    # filled by the server
+    admitted: float = -1.0
+    finished: float = -1.0
+    probs: Optional[np.ndarray] = None
+    norm: float = float("nan")
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+@dataclass
+class _Active:
+    req: Request
+    state: "qs.State"
+    offset: int
+    chunks: List["qs.Circuit"]
+    pos: int = 0
+    stream: object = None
+
+
+class BuddyArena:
+    """Power-of-two sub-allocator over one device allocation (state sizes
+    are powers of two, so a freed state's block merges back with its buddy).
+    Host-side bookkeeping only; the memory is one torch uint8 tensor."""
+
+    def __init__(self, total_bytes: int, min_bytes: int = 1 << 12):
+        import torch
+
+        self.top = max(int(total_bytes).bit_length() - 1, min_bytes.bit_length() - 1)
+        self.min_order = min_bytes.bit_length() - 1
+        self.tensor = torch.empty(1 << self.top, dtype=torch.uint8, device="cuda")
+        self.base = self.tensor.data_ptr()
+        self.free = {o: set() for o in range(self.min_order, self.top + 1)}
+        self.free[self.top].add(0)
+
+    @property
+    def capacity(self) -> int:
+        return 1 << self.top
+
+    def alloc(self, nbytes: int) -> Optional[int]:
+        order = max(self.min_order, (int(nbytes) - 1).bit_length())
+        o = order
+        while o <= self.top and not self.free[o]:
+            o += 1
+        if o > self.top:
+            return None
+        off = min(self.free[o])
+        self.free[o].remove(off)
+        while o > order:  # split, keeping the lower half
+            o -= 1
+            self.free[o].add(off + (1 << o))
+        return off
+
+    def release(self, off: int, nbytes: int):
+        o = max(self.min_order, (int(nbytes) - 1).bit_length())
+        while o < self.top:
+            buddy = off ^ (1 << o)
+            if buddy not in self.free[o]:
+                break
+            self.free[o].remove(buddy)
+            off = min(off, buddy)
+            o += 1
+        self.free[o].add(off)
+
+
+class Server:
+    def __init__(self, dtype: int = qs.QS_C128, hbm_budget_bytes: int = 64 << 30, max_resident: int = 256,
+                 small_n: int = 16, chunk_gates: int = 128, max_fuse: int = 0, result_qubits: int = 8):
+        import torch
+
+        self.torch = torch
+        self.dtype = dtype
+        self.amp_bytes = 8 if dtype == qs.QS_C64 else 16
+        self.arena = BuddyArena(hbm_budget_bytes)
+        self.max_resident = int(max_resident)
+        self.small_n = int(small_n)
+        self.chunk_gates = int(chunk_gates)
+        self.max_fuse = int(max_fuse)
+        self.result_qubits = int(result_qubits)
+        self.small_stream = torch.cuda.Stream()
+        self.streams = [torch.cuda.Stream() for _ in range(4)]
+        self.result_stream = torch.cuda.Stream()
+        self.result_buf = torch.zeros((1 << self.result_qubits) + 1, dtype=torch.float64, device="cuda")
+        self._next_stream = 0
+        self.used = 0
+        self.active: Dict[int, _Active] = {}
+        self.pending: List = []          # heap of (arrival, rid, Request)
+        self.done: List[Request] = []
+        self.ticks = 0
+        self.peak_used = 0
+
+    # -- requests ------------------------------------------------------
+    def footprint(self, n: int) -> int:
+        return self.amp_bytes << n
+
+    def submit(self, req: Request):
+        if self.footprint(req.n) > self.arena.capacity:
+            raise ValueError(f"request {req.rid}: {req.n} qubits exceed the HBM budget")
+        heapq.heappush(self.pending, (req.arrival, req.rid, req))
+
+    def _chunks(self, gates) -> List["qs.Circuit"]:
+        return [qs.Circuit(gates[i:i + self.chunk_gates]) for i in range(0, len(gates), self.chunk_gates)] or \
+            [qs.Circuit([])]
+
+    def _admit(self, now: float):
+        while self.pending and self.pending[0][0] <= now and len(self.active) < self.max_resident:
+            req = self.pending[0][2]
+            fp = self.footprint(req.n)
+            off = self.arena.alloc(fp)
+            if off is None:
+                break  # admission by footprint: wait for memory to free up
+            heapq.heappop(self.pending)
+            if req.n <= self.small_n:
+                stream = self.small_stream
+            else:
+                stream = self.streams[self._next_stream % len(self.streams)]
+                self._next_stream += 1
+            h = qs.qs_wrap(req.n, self.dtype, self.arena.base + off, stream.cuda_stream)
+            st = qs.State(req.n, self.dtype, handle=h)
+            qs.qs_init_basis(st.h, 0)
+            req.admitted = now
+            self.active[req.rid] = _Active(req, st, off, self._chunks(req.gates), 0, stream)
+            self.used += fp
+            self.peak_used = max(self.peak_used, self.used)
+
+    # -- one scheduler tick ---------------------------------------------
+    def _tick(self):
+        small = [a for a in self.active.values() if a.req.n <= self.small_n]
+        large = [a for a in self.active.values() if a.req.n > self.small_n]
+        if small:
+            qs.qs_batch_run([a.state.h for a in small], [a.chunks[a.pos] for a in small])
+            for a in small:
+                a.pos += 1
+        for a in large:
+            qs.qs_fuse_run(a.state.h, a.chunks[a.pos], qs.run_opts(max_fuse=self.max_fuse))
+            a.pos += 1
+        self.ticks += 1
+
+    def _read_result(self, a: _Active):
+        """Marginals of the lowest qubits and the norm, computed without
+        allocation on one result stream (so result reads never overlap)."""
+        k = min(self.result_qubits, a.req.n)
+        rs = self.result_stream
+        rs.wait_stream(a.stream)
+        ptr = self.arena.base + a.offset
+        qs.qs_probs_noalloc(ptr, a.req.n, self.dtype, list(range(k)), self.result_buf.data_ptr(), rs.cuda_stream)
+        qs.qs_probs_noalloc(ptr, a.req.n, self.dtype, [], self.result_buf.data_ptr() + 8 * (1 << k), rs.cuda_stream)
+        with self.torch.cuda.stream(rs):
+            host = self.result_buf[: (1 << k) + 1].to("cpu", non_blocking=False)
+        vals = host.numpy()
+        a.req.probs = vals[: 1 << k].copy()
+        a.req.norm = float(vals[1 << k])
+
+    def _complete(self, clock):
+        for rid in [r for r, a in self.active.items() if a.pos >= len(a.chunks)]:
+            a = self.active.pop(rid)
+            self._read_result(a)
+            a.req.finished = clock()
+            # the state's memory returns to the arena only after the reads
+            self.result_stream.synchronize()
+            a.state.close()
+            self.arena.release(a.offset, self.footprint(a.req.n))
+            self.used -= self.footprint(a.req.n)
+            self.done.append(a.req)
+
+    def run(self, clock=None) -> List[Request]:
+        """Serve every submitted request; arrivals are honoured against
+        ``clock`` (seconds, default: wall time since this call)."""
+        t0 = time.perf_counter()
+        clock = clock or (lambda: time.perf_counter() - t0)
+        while self.pending or self.active:
+            now = clock()
+            self._admit(now)
+            if not self.active:
+                wait = self.pending[0][0] - clock()  # idle until the next arrival
+                if wait > 0:
+                    time.sleep(min(wait, 0.01))
+                continue
+            self._tick()
+            self._complete(clock)
+        self.torch.cuda.synchronize()
+        return self.done
+
+
+# ---------------------------------------------------------------------------
+# Request streams shaped like the serving workload
+# ---------------------------------------------------------------------------
+def make_requests(count: int, seed: int, n_min: int = 12, n_max: int = 30, rate: float = 0.0,
+                  grover_cap: int = 16, mix=(0.4, 0.3, 0.3)) -> List[Request]:
+    """``count`` requests, qubit count log-uniform on [n_min, n_max]
+    (n = round(2^U(log2 n_min, log2 n_max))), kinds 40% RQC depth 20 / 30%
+    QFT of a random basis state / 30% Grover (iterations capped at
+    ``grover_cap``); Poisson arrivals at ``rate`` per second (0: all at t=0)."""
+    from workloads import circuits as W
+
+    rng = W.rng_for(seed)
+    reqs = []
+    t = 0.0
+    for i in range(count):
+        u = rng.uniform(math.log2(n_min), math.log2(n_max))
+        n = int(round(2.0 ** u))
+        r = rng.random()
+        if r < mix[0]:
+            kind, gates = "rqc", W.rqc(n, 20, seed=seed * 100003 + i)
+        elif r < mix[0] + mix[1]:
+            x = int(rng.integers(1 << n))
+            kind, gates = "qft", [W.X(q) for q in range(n) if (x >> q) & 1] + W.qft(list(range(n)))
+        else:
+            marked = int(rng.integers(1 << n))
+            kind, gates = "grover", W.grover(n, marked, min(W.grover_iterations(n), grover_cap))
+        if rate > 0:
+            t += rng.exponential(1.0 / rate)
+        reqs.append(Request(rid=i, n=n, gates=gates, arrival=t, kind=kind))
+    return reqs
+
+
+def summarize(done: List[Request], wall_s: float) -> dict:
+    lat = np.array([r.latency for r in done]) if done else np.zeros(1)
+    return {"requests": len(done), "wall_s": wall_s, "circuits_per_s": len(done) / wall_s if wall_s > 0 else 0.0,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3)}
