@@ -185,23 +185,9 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_batch(const BatchArgs<TP> a
     const BatchBlock& b = a.blocks[d.block];
     const uint32_t tile_amps = 1u << (b.L + b.m);
     Sm* t = reinterpret_cast<Sm*>(smem + (size_t)s * kMaxTileBytes);
-    if constexpr (!std::is_same<Glob, Sm>::value) {
-      for (uint32_t e = tid; e < tile_amps; e += kTileConsumers) t[e] = TP::to_sm(reinterpret_cast<Glob*>(t)[e]);
-      consumers_sync();
-    }
     const uint64_t base = tile_base(d.tau, b.L, b.m, b.base_high);
-    const TileOp* ops = a.ops + b.op0;
-    const typename TP::M::Coef* coefs = a.coefs + b.coef0;
-    const uint8_t* perm = a.perm + b.perm0;
-    for (int o = 0; o < b.nops; ++o) {
-      const TileOp& op = ops[o];
-      if ((base & op.gmask) != op.gpat) continue;
-      apply_op<TP>(t, op, coefs, perm, tile_amps, base, tid);
-      consumers_sync();
-    }
-    if constexpr (!std::is_same<Glob, Sm>::value) {
-      for (uint32_t e = tid; e < tile_amps; e += kTileConsumers) reinterpret_cast<Glob*>(t)[e] = TP::from_sm(t[e]);
-    }
+    consume_tile<TP>(reinterpret_cast<unsigned char*>(t), a.ops + b.op0, b.nops, a.coefs + b.coef0,
+                     a.perm + b.perm0, b.L + b.m, base, tid);
     fence_async_smem();
     mbar_arrive(&done[s]);
   }
@@ -273,6 +259,7 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
       }
       if (emitted == 0) return fail(QS_ERR_UNSUPPORTED, "batch state %d: gate %zu could not be placed", i, next);
       if (bo.ops.empty()) continue;
+      bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits);
       BatchBlock b;
       std::memset(&b, 0, sizeof(b));
       b.L = geom.L;

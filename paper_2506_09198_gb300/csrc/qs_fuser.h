@@ -142,14 +142,13 @@ struct PlanBuilder {
     return op;
   }
 
-  // Local controls are inserted as fixed 1s; controls on free qubits become
-  // the op's tile predicate.
-  void controls(TileOp& op, uint64_t ctrl, std::vector<int>& ins, uint32_t& fixed) const {
+  // Local controls form the op's local mask; controls on free qubits
+  // become its tile predicate.
+  void controls(TileOp& op, uint64_t ctrl) const {
     for (int q = 0; q < 64; ++q) {
       if (!((ctrl >> q) & 1ull)) continue;
       if (local_of[q] >= 0) {
-        ins.push_back(local_of[q]);
-        fixed |= 1u << local_of[q];
+        op.lmask |= 1u << local_of[q];
       } else {
         op.gmask |= 1ull << q;
         op.gpat |= 1ull << q;
@@ -157,17 +156,8 @@ struct PlanBuilder {
     }
   }
 
-  static bool set_positions(TileOp& op, std::vector<int> ins, uint32_t fixed) {
-    if ((int)ins.size() > kTileMaxPos) return false;
-    std::sort(ins.begin(), ins.end());
-    op.npos = (uint8_t)ins.size();
-    for (size_t j = 0; j < ins.size(); ++j) op.himask[j] = ~((1u << ins[j]) - 1u);
-    op.ifixed = fixed;
-    return true;
-  }
-
-  uint16_t add_coefs(const double* z, int count) {
-    const uint16_t at = (uint16_t)out->coefs.size();
+  uint32_t add_coefs(const double* z, int count) {
+    const uint32_t at = (uint32_t)out->coefs.size();
     for (int j = 0; j < count; ++j) out->coefs.push_back(P::make_coef(z[2 * j], z[2 * j + 1]));
     return at;
   }
@@ -175,20 +165,17 @@ struct PlanBuilder {
   bool phase(uint64_t mask, uint64_t pattern, const double* c) {
     if (!room(1, 1, 0)) return false;
     TileOp op = blank();
-    std::vector<int> ins;
-    uint32_t fixed = 0;
     for (int q = 0; q < 64; ++q) {
       if (!((mask >> q) & 1ull)) continue;
       const bool one = (pattern >> q) & 1ull;
       if (local_of[q] >= 0) {
-        ins.push_back(local_of[q]);
-        if (one) fixed |= 1u << local_of[q];
+        op.lmask |= 1u << local_of[q];
+        if (one) op.lpat |= 1u << local_of[q];
       } else {
         op.gmask |= 1ull << q;
         if (one) op.gpat |= 1ull << q;
       }
     }
-    if (!set_positions(op, ins, fixed)) return false;
     if (is_c(c, -1, 0)) {
       op.kind = TOP_NEG;
     } else {
@@ -219,10 +206,7 @@ struct PlanBuilder {
     TileOp op = blank();
     op.kind = TOP_DIAG;
     op.k = (uint8_t)k;
-    std::vector<int> ins;
-    uint32_t fixed = 0;
-    controls(op, ctrl, ins, fixed);
-    if (!set_positions(op, ins, fixed)) return false;
+    controls(op, ctrl);
     int nl = 0;
     for (int j = 0; j < k; ++j) {
       const int lq = local_of[targets[j]];
@@ -246,10 +230,7 @@ struct PlanBuilder {
     TileOp op = blank();
     op.kind = kind;
     op.tpos[0] = (uint8_t)local_of[t];
-    std::vector<int> ins{local_of[t]};
-    uint32_t fixed = 0;
-    controls(op, ctrl, ins, fixed);
-    if (!set_positions(op, ins, fixed)) return false;
+    controls(op, ctrl);
     if (U) op.coef = add_coefs(U, 4);
     out->ops.push_back(op);
     return true;
@@ -261,10 +242,7 @@ struct PlanBuilder {
     op.kind = TOP_DENSE2;
     op.tpos[0] = (uint8_t)local_of[t0];
     op.tpos[1] = (uint8_t)local_of[t1];
-    std::vector<int> ins{local_of[t0], local_of[t1]};
-    uint32_t fixed = 0;
-    controls(op, ctrl, ins, fixed);
-    if (!set_positions(op, ins, fixed)) return false;
+    controls(op, ctrl);
     op.coef = add_coefs(U, 16);
     out->ops.push_back(op);
     return true;
@@ -276,16 +254,8 @@ struct PlanBuilder {
     op.kind = TOP_PERM;
     op.k = (uint8_t)k;
     for (int j = 0; j < k; ++j) op.tpos[j] = (uint8_t)local_of[targets[j]];
-    for (int q = 0; q < 64; ++q) {
-      if (!((ctrl >> q) & 1ull)) continue;
-      if (local_of[q] >= 0) {
-        op.lmask |= 1u << local_of[q];
-      } else {
-        op.gmask |= 1ull << q;
-        op.gpat |= 1ull << q;
-      }
-    }
-    op.ptab = (uint16_t)out->perm.size();
+    controls(op, ctrl);
+    op.ptab = (uint32_t)out->perm.size();
     const size_t at = out->perm.size();
     out->perm.resize(at + (1u << k));
     for (int v = 0; v < (1 << k); ++v) out->perm[at + p[v]] = (uint8_t)v;  // inverse table
@@ -343,6 +313,71 @@ struct PlanBuilder {
     return false;
   }
 };
+
+// Local bits that must be register bits for an op (dense gates and moves).
+inline uint32_t reg_need(const TileOp& op) {
+  if (op.kind == TOP_DENSE1 || op.kind == TOP_XSWAP || op.kind == TOP_Y) return 1u << op.tpos[0];
+  if (op.kind == TOP_DENSE2) return (1u << op.tpos[0]) | (1u << op.tpos[1]);
+  return 0u;
+}
+
+// Insert layout changes so that every dense op finds its targets in
+// registers, and rewrite those targets as register bit indices.  A new layout
+// takes the targets of the op that needs it plus those of the following ops,
+// in order, while they fit in rb register bits; free register slots take the
+// highest remaining local bits (the low bits stay thread bits, so shared
+// memory accesses of a warp fall on consecutive amplitudes).
+inline std::vector<TileOp> schedule_layouts(const std::vector<TileOp>& ops, int tile_log, int reg_bits) {
+  const int rb = tile_log < reg_bits ? tile_log : reg_bits;
+  std::vector<TileOp> out;
+  out.reserve(ops.size() + 8);
+  uint32_t cur = 0;
+  int pos_of[32];
+  bool have = false;
+  auto make_layout = [&](size_t i) {
+    uint32_t set = 0;
+    int cnt = 0;
+    for (size_t j = i; j < ops.size(); ++j) {
+      const uint32_t need = reg_need(ops[j]);
+      if (!need) continue;
+      const uint32_t u = set | need;
+      if (__builtin_popcount(u) > rb) break;
+      set = u;
+      cnt = __builtin_popcount(set);
+    }
+    for (int b = tile_log - 1; b >= 0 && cnt < rb; --b)
+      if (!((set >> b) & 1u)) {
+        set |= 1u << b;
+        ++cnt;
+      }
+    TileOp lay;
+    std::memset(&lay, 0, sizeof(lay));
+    lay.kind = TOP_LAYOUT;
+    lay.k = (uint8_t)rb;
+    int j = 0;
+    for (int b = 0; b < tile_log; ++b)
+      if ((set >> b) & 1u) {
+        lay.tpos[j] = (uint8_t)b;
+        pos_of[b] = j;
+        ++j;
+      }
+    cur = set;
+    have = true;
+    out.push_back(lay);
+  };
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const uint32_t need = reg_need(ops[i]);
+    if (!have || (need & ~cur)) make_layout(i);
+    TileOp op = ops[i];
+    if (need) {
+      op.tpos[0] = (uint8_t)pos_of[ops[i].tpos[0]];
+      if (op.kind == TOP_DENSE2) op.tpos[1] = (uint8_t)pos_of[ops[i].tpos[1]];
+    }
+    out.push_back(op);
+  }
+  if (!have) make_layout(0);
+  return out;
+}
 
 // Estimated pool use of one gate.
 inline void pool_need(const FGate& g, int* coefs, int* perm_bytes) {

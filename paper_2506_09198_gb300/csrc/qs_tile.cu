@@ -125,20 +125,9 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_tile(typename TP::Glob* __r
     const bool ok = mbar_wait(&full[s], (j / kStages) & 1u, err);
     if (consumers_any(!ok)) break;
     Sm* t = reinterpret_cast<Sm*>(smem + (size_t)s * tile_bytes);
-    if constexpr (!std::is_same<Glob, Sm>::value) {
-      for (uint32_t e = tid; e < tile_amps; e += kTileConsumers) t[e] = TP::to_sm(reinterpret_cast<Glob*>(t)[e]);
-      consumers_sync();
-    }
     const uint64_t base = tile_base(tau, plan.L, plan.m, plan.base_high);
-    for (int o = 0; o < plan.nops; ++o) {
-      const TileOp& op = plan.ops[o];
-      if ((base & op.gmask) != op.gpat) continue;
-      apply_op<TP>(t, op, plan.coefs, plan.perm, tile_amps, base, tid);
-      consumers_sync();
-    }
-    if constexpr (!std::is_same<Glob, Sm>::value) {
-      for (uint32_t e = tid; e < tile_amps; e += kTileConsumers) reinterpret_cast<Glob*>(t)[e] = TP::from_sm(t[e]);
-    }
+    consume_tile<TP>(reinterpret_cast<unsigned char*>(t), plan.ops, plan.nops, plan.coefs, plan.perm,
+                     plan.L + plan.m, base, tid);
     fence_async_smem();
     mbar_arrive(&done[s]);
   }
@@ -219,7 +208,8 @@ qs_status run_blocks(qs_state s, const std::vector<FGate>& gates, int max_high) 
   using Coef = typename TP::M::Coef;
   const int n = s->n;
   const int min_chunk = sizeof(typename TP::Glob) == 16 ? kMinChunkLog128 : kMinChunkLog64;
-  const Limits lim{kTileMaxOps, kTileMaxCoefs, kTileMaxPermBytes};
+  // Scheduling adds at most one layout change per gate.
+  const Limits lim{kTileMaxOps / 2, kTileMaxCoefs, kTileMaxPermBytes};
   static thread_local std::vector<unsigned char> plan_mem;
   plan_mem.resize(sizeof(TilePlan<Coef>));
   TilePlan<Coef>* plan = reinterpret_cast<TilePlan<Coef>*>(plan_mem.data());
@@ -256,6 +246,7 @@ qs_status run_blocks(qs_state s, const std::vector<FGate>& gates, int max_high) 
       continue;
     }
     if (!bo.ops.empty()) {
+      bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits);
       fill_plan(plan, n, bo);
       qs_status st = launch_plan<TP>(s, *plan);
       if (st != QS_OK) return st;

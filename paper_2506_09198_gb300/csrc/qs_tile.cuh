@@ -1,5 +1,5 @@
-// Fused-block ("tile") engine: plan layout shared by the host fuser and the
-// kernel.
+// Fused-block ("tile") engine: op and plan layout shared by the host fuser
+// and the kernels.
 //
 // A tile is 2^(L+m) amplitudes: 2^m chunks of 2^L contiguous amplitudes,
 // chunk c at global offset base + sum_j bit_j(c) 2^hq[j].  Local index
@@ -16,39 +16,45 @@
 
 namespace qs {
 
-constexpr int kTileMaxOps = 40;
+constexpr int kTileMaxOps = 96;  // scheduled ops (gates plus layout changes) per plan
 constexpr int kTileMaxHigh = 8;
 constexpr int kTileMaxChunks = 1 << kTileMaxHigh;
 constexpr int kTileMaxCoefs = 320;
 constexpr int kTileMaxPermBytes = 512;
-constexpr int kTileMaxPos = 14;  // inserted local bit positions per op
 
+// Inside a tile every consumer thread holds 2^RB amplitudes in registers.
+// A layout names the RB local bits that index a thread's registers (in
+// order); the remaining local bits, ascending, are the thread index.  Gates
+// whose targets are register bits run without communication; a layout change
+// moves the tile through shared memory.  The host schedules layout changes
+// (TOP_LAYOUT) so that every dense gate finds its targets in registers.
 enum TileOpKind : uint8_t {
-  TOP_DENSE1 = 0,  // 2x2 on local bit tpos[0]
-  TOP_DENSE2 = 1,  // 4x4 on local bits tpos[0], tpos[1] (index b0 + 2 b1)
-  TOP_PHASE = 2,   // multiply the amplitudes that match a bit pattern by one coefficient
-  TOP_NEG = 3,     // same with coefficient -1 (sign flip)
-  TOP_DIAG = 4,    // d[s], s from local target bits and tile-constant bits
-  TOP_XSWAP = 5,   // swap pair partners on local bit tpos[0]
-  TOP_Y = 6,       // up' = -i lo, lo' = i up
-  TOP_PERM = 7     // index permutation of local target bits (inverse table)
+  TOP_LAYOUT = 0,  // new layout: register bit j = local bit tpos[j]
+  TOP_DENSE1 = 1,  // 2x2 on register bit tpos[0]
+  TOP_DENSE2 = 2,  // 4x4 on register bits tpos[0], tpos[1] (index b0 + 2 b1)
+  TOP_XSWAP = 3,   // swap pair partners on register bit tpos[0]
+  TOP_Y = 4,       // up' = -i lo, lo' = i up on register bit tpos[0]
+  TOP_PHASE = 5,   // multiply amplitudes with (lambda & lmask) == lpat by one coefficient
+  TOP_NEG = 6,     // same with coefficient -1 (sign flip)
+  TOP_DIAG = 7,    // d[s]: s from local targets tpos[0..nloc) (sub-register bits tj) and tile bits gq
+  TOP_PERM = 8     // permutation of local targets tpos[0..k), through shared memory
 };
 
+// Before scheduling (host), dense gates carry local bit positions in tpos;
+// the scheduler rewrites them to register bit indices.
 struct TileOp {
   uint8_t kind;
-  uint8_t k;                  // DIAG / PERM: number of targets
-  uint8_t npos;               // positions inserted to enumerate items
-  uint8_t nloc;               // DIAG: local targets
-  uint32_t himask[kTileMaxPos];  // ~((1 << pos) - 1) for the ascending local positions inserted
-                                 // (targets' 0s, controls' 1s)
-  uint8_t tpos[8];            // local positions of targets
-  uint8_t tj[8];              // DIAG: sub-register bit of each local target
-  uint8_t gq[8];              // DIAG: global qubit of target j when it is not local, else 0xFF
-  uint32_t ifixed;            // bits set after insertion (local controls / pattern ones)
-  uint32_t lmask;             // PERM: local control mask
-  uint64_t gmask, gpat;       // the op acts on a tile iff (base & gmask) == gpat
-  uint16_t coef;              // first coefficient in the plan's pool
-  uint16_t ptab;              // PERM: byte offset of the inverse table
+  uint8_t k;        // DIAG / PERM: number of targets; LAYOUT: register bits
+  uint8_t nloc;     // DIAG: local targets
+  uint8_t pad0;
+  uint8_t tpos[8];
+  uint8_t tj[8];    // DIAG: sub-register bit of each local target
+  uint8_t gq[8];    // DIAG: global qubit of target j when not local, else 0xFF
+  uint32_t lmask;   // local control mask (PHASE/NEG: pattern mask)
+  uint32_t lpat;    // PHASE/NEG: local pattern
+  uint64_t gmask, gpat;  // the op acts on a tile iff (base & gmask) == gpat
+  uint32_t coef;    // first coefficient in the pool
+  uint32_t ptab;    // PERM: byte offset of the inverse table
 };
 
 template <class Coef>

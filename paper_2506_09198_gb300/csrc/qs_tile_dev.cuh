@@ -97,7 +97,7 @@ struct TileF32 {
   using Glob = float2;
   using Sm = float2;
   static constexpr int kTileLog = 12;  // 4096 amplitudes, 32 KB
-  static constexpr int kIlp = 4;
+  static constexpr int kRegBits = 4;  // 16 amplitudes per thread
   static __device__ __forceinline__ Sm to_sm(Glob g) { return g; }
   static __device__ __forceinline__ Glob from_sm(Sm s) { return s; }
   static __device__ __forceinline__ M::Val val(Sm s) { return M::load(s); }
@@ -121,7 +121,7 @@ struct TileF64 {
   using Glob = double2;
   using Sm = double2;
   static constexpr int kTileLog = 11;  // 2048 amplitudes, 32 KB
-  static constexpr int kIlp = 2;
+  static constexpr int kRegBits = 3;  // 8 amplitudes per thread
   static __device__ __forceinline__ Sm to_sm(Glob g) { return g; }
   static __device__ __forceinline__ Glob from_sm(Sm s) { return s; }
   static __device__ __forceinline__ M::Val val(Sm s) { return M::load(s); }
@@ -138,7 +138,7 @@ struct TileDF {
   using Glob = double2;
   using Sm = float4;
   static constexpr int kTileLog = 11;
-  static constexpr int kIlp = 2;
+  static constexpr int kRegBits = 3;  // 8 amplitudes per thread
   static __device__ __forceinline__ Sm to_sm(Glob g) {
     Sm s;
     d2ff(g.x, s.x, s.z);
@@ -173,27 +173,8 @@ struct TileDF {
 };
 
 // ---------------------------------------------------------------------------
-// Kernel
+// Register-resident tile consumer
 // ---------------------------------------------------------------------------
-// Local item index -> local amplitude index: insert a zero at each listed
-// position (adding the bits at and above a position shifts them up by one),
-// then set the fixed bits.  The first four masks live in registers.
-struct LocalExpand {
-  int npos;
-  uint32_t h0, h1, h2, h3, fixed;
-  const TileOp* op;
-  __device__ __forceinline__ explicit LocalExpand(const TileOp& o)
-      : npos(o.npos), h0(o.himask[0]), h1(o.himask[1]), h2(o.himask[2]), h3(o.himask[3]), fixed(o.ifixed), op(&o) {}
-  __device__ __forceinline__ uint32_t operator()(uint32_t i) const {
-    if (npos > 0) i += i & h0;
-    if (npos > 1) i += i & h1;
-    if (npos > 2) i += i & h2;
-    if (npos > 3) i += i & h3;
-    for (int p = 4; p < npos; ++p) i += i & op->himask[p];
-    return i | fixed;
-  }
-};
-
 // Global index of a tile's first amplitude: the tile number spread over the
 // free qubits (zeros inserted at the high tile qubits, ascending).
 __device__ __forceinline__ uint64_t tile_base(uint64_t tau, int L, int m, const uint64_t* base_high) {
@@ -203,148 +184,258 @@ __device__ __forceinline__ uint64_t tile_base(uint64_t tau, int L, int m, const 
 }
 
 template <class TP>
-__device__ __forceinline__ void apply_op(typename TP::Sm* __restrict__ t, const TileOp& op,
-                                         const typename TP::M::Coef* __restrict__ coefs,
-                                         const uint8_t* __restrict__ perm_tables, uint32_t tile_amps, uint64_t base,
-                                         int tid) {
+struct RegTile {
+  static constexpr int RB = TP::kRegBits;
+  static constexpr int R = 1 << RB;
   using Sm = typename TP::Sm;
+  using Glob = typename TP::Glob;
   using Val = typename TP::M::Val;
   using Coef = typename TP::M::Coef;
-  constexpr int U = TP::kIlp;  // independent items in flight per thread
-  const Coef* cf = coefs + op.coef;
-  const LocalExpand ex(op);
-  const uint32_t items = tile_amps >> op.npos;
-  const uint32_t step = (uint32_t)kTileConsumers * U;
-  switch (op.kind) {
-    case TOP_DENSE1: {
-      const uint32_t tb = 1u << op.tpos[0];
-      Coef c[4];
+
+  Sm v[R];
+  uint32_t pbit[RB];  // local index bit of register bit j (0 when unused)
+  uint32_t toff;      // local index bits of this thread
+  int reff;           // registers in use (fewer for tiles smaller than 2^RB)
+  bool active;        // this thread holds amplitudes
+
+  // Local index bits of register r (r is a compile-time constant in the
+  // unrolled loops, so this folds to a few ORs).
+  __device__ __forceinline__ uint32_t roff(int r) const {
+    uint32_t o = 0;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) c[j] = cf[j];
-      for (uint32_t it0 = tid; it0 < items; it0 += step) {
-        uint32_t ii[U];
-        Sm a[U], b[U];
+    for (int j = 0; j < RB; ++j)
+      if ((r >> j) & 1) o |= pbit[j];
+    return o;
+  }
+
+  // Set the layout: register bit j is local bit pos[j]; the other local
+  // bits, ascending, take the thread index bits.
+  __device__ __forceinline__ void set_layout(const uint8_t* pos, int rb, int tile_log, int tid) {
+    uint32_t regmask = 0;
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (it0 + u * kTileConsumers < items) {
-            ii[u] = ex(it0 + u * kTileConsumers);
-            a[u] = t[ii[u]];
-            b[u] = t[ii[u] | tb];
-          }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (it0 + u * kTileConsumers < items) {
-            const Val v[2] = {TP::val(a[u]), TP::val(b[u])};
-            t[ii[u]] = TP::template mac<2>(c, v);
-            t[ii[u] | tb] = TP::template mac<2>(c + 2, v);
-          }
-      }
-      break;
+    for (int j = 0; j < RB; ++j) {
+      pbit[j] = j < rb ? (1u << pos[j]) : 0u;
+      regmask |= pbit[j];
     }
-    case TOP_DENSE2: {
-      const uint32_t b0 = 1u << op.tpos[0], b1 = 1u << op.tpos[1];
-      for (uint32_t it = tid; it < items; it += kTileConsumers) {
-        const uint32_t i = ex(it);
-        const Val v[4] = {TP::val(t[i]), TP::val(t[i | b0]), TP::val(t[i | b1]), TP::val(t[i | b0 | b1])};
-        t[i] = TP::template mac<4>(cf, v);
-        t[i | b0] = TP::template mac<4>(cf + 4, v);
-        t[i | b1] = TP::template mac<4>(cf + 8, v);
-        t[i | b0 | b1] = TP::template mac<4>(cf + 12, v);
-      }
-      break;
+    uint32_t t = 0;
+    int jt = 0;
+    for (int b = 0; b < tile_log; ++b) {
+      if ((regmask >> b) & 1u) continue;
+      if ((tid >> jt) & 1) t |= 1u << b;
+      ++jt;
     }
-    case TOP_PHASE: {
-      const Coef c = cf[0];
-      for (uint32_t it0 = tid; it0 < items; it0 += step) {
-        uint32_t ii[U];
-        Sm a[U];
+    toff = t;
+    reff = 1 << rb;
+    active = (tid >> (tile_log - rb)) == 0;
+  }
+
+  __device__ __forceinline__ void read_glob(const unsigned char* smem) {
+    const Glob* g = reinterpret_cast<const Glob*>(smem);
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (it0 + u * kTileConsumers < items) {
-            ii[u] = ex(it0 + u * kTileConsumers);
-            a[u] = t[ii[u]];
-          }
+    for (int r = 0; r < R; ++r)
+      if (r < reff && active) v[r] = TP::to_sm(g[toff | roff(r)]);
+  }
+  __device__ __forceinline__ void read_sm(const unsigned char* smem) {
+    const Sm* t = reinterpret_cast<const Sm*>(smem);
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (it0 + u * kTileConsumers < items) {
-            const Val v = TP::val(a[u]);
-            t[ii[u]] = TP::template mac<1>(&c, &v);
-          }
-      }
-      break;
-    }
-    case TOP_NEG: {
-      for (uint32_t it = tid; it < items; it += kTileConsumers) {
-        const uint32_t i = ex(it);
-        t[i] = TP::neg(t[i]);
-      }
-      break;
-    }
-    case TOP_DIAG: {
-      uint32_t sg = 0;
-      for (int j = 0; j < op.k; ++j)
-        if (op.gq[j] != 0xFF) sg |= (uint32_t)((base >> op.gq[j]) & 1ull) << j;
-      for (uint32_t it0 = tid; it0 < items; it0 += step) {
-        uint32_t ii[U];
-        Sm a[U];
+    for (int r = 0; r < R; ++r)
+      if (r < reff && active) v[r] = t[toff | roff(r)];
+  }
+  __device__ __forceinline__ void write_sm(unsigned char* smem) const {
+    Sm* t = reinterpret_cast<Sm*>(smem);
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (it0 + u * kTileConsumers < items) {
-            ii[u] = ex(it0 + u * kTileConsumers);
-            a[u] = t[ii[u]];
-          }
+    for (int r = 0; r < R; ++r)
+      if (r < reff && active) t[toff | roff(r)] = v[r];
+  }
+  __device__ __forceinline__ void write_glob(unsigned char* smem) const {
+    Glob* g = reinterpret_cast<Glob*>(smem);
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (it0 + u * kTileConsumers < items) {
-            uint32_t sidx = sg;
-            for (int j = 0; j < op.nloc; ++j) sidx |= ((ii[u] >> op.tpos[j]) & 1u) << op.tj[j];
-            const Val v = TP::val(a[u]);
-            t[ii[u]] = TP::template mac<1>(cf + sidx, &v);
-          }
-      }
-      break;
-    }
-    case TOP_XSWAP:
-    case TOP_Y: {
-      const uint32_t tb = 1u << op.tpos[0];
-      const bool y = op.kind == TOP_Y;
-      for (uint32_t it = tid; it < items; it += kTileConsumers) {
-        const uint32_t i = ex(it);
-        const Sm a = t[i], b = t[i | tb];
-        t[i] = y ? TP::mul_minus_i(b) : b;
-        t[i | tb] = y ? TP::mul_i(a) : a;
-      }
-      break;
-    }
-    case TOP_PERM: {
-      // Two phases through registers: gather every destination's source,
-      // then write, so the permutation is applied in place.
-      constexpr int kMaxPer = (1 << TP::kTileLog) / kTileConsumers;
-      Sm buf[kMaxPer];
-      const uint8_t* inv = perm_tables + op.ptab;
+    for (int r = 0; r < R; ++r)
+      if (r < reff && active) g[toff | roff(r)] = TP::from_sm(v[r]);
+  }
+
+  template <int K>
+  __device__ __forceinline__ void dense1(const Coef* cf, uint32_t lmask) {
+    Coef c[4];
 #pragma unroll
-      for (int r = 0; r < kMaxPer; ++r) {
-        const uint32_t d = (uint32_t)tid + (uint32_t)r * kTileConsumers;
-        if (d < tile_amps) {
-          uint32_t src = d;
-          if ((d & op.lmask) == op.lmask) {
-            uint32_t sidx = 0;
-            for (int j = 0; j < op.k; ++j) sidx |= ((d >> op.tpos[j]) & 1u) << j;
-            const uint32_t sv = inv[sidx];
-            for (int j = 0; j < op.k; ++j) src = (src & ~(1u << op.tpos[j])) | (((sv >> j) & 1u) << op.tpos[j]);
-          }
-          buf[r] = t[src];
-        }
-      }
-      consumers_sync();
+    for (int j = 0; j < 4; ++j) c[j] = cf[j];
 #pragma unroll
-      for (int r = 0; r < kMaxPer; ++r) {
-        const uint32_t d = (uint32_t)tid + (uint32_t)r * kTileConsumers;
-        if (d < tile_amps) t[d] = buf[r];
-      }
-      break;
+    for (int r = 0; r < R; ++r) {
+      if (r & (1 << K)) continue;
+      if (r >= reff) continue;
+      if (((toff | roff(r)) & lmask) != lmask) continue;
+      const Val x[2] = {TP::val(v[r]), TP::val(v[r | (1 << K)])};
+      v[r] = TP::template mac<2>(c, x);
+      v[r | (1 << K)] = TP::template mac<2>(c + 2, x);
     }
   }
+
+  template <int K>
+  __device__ __forceinline__ void xswap(bool y, uint32_t lmask) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r & (1 << K)) continue;
+      if (r >= reff) continue;
+      if (((toff | roff(r)) & lmask) != lmask) continue;
+      const Sm a = v[r], b = v[r | (1 << K)];
+      v[r] = y ? TP::mul_minus_i(b) : b;
+      v[r | (1 << K)] = y ? TP::mul_i(a) : a;
+    }
+  }
+
+  template <int K0, int K1>
+  __device__ __forceinline__ void dense2(const Coef* cf, uint32_t lmask) {
+    constexpr int B0 = 1 << K0, B1 = 1 << K1;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r & (B0 | B1)) continue;
+      if (r >= reff) continue;
+      if (((toff | roff(r)) & lmask) != lmask) continue;
+      const Val x[4] = {TP::val(v[r]), TP::val(v[r | B0]), TP::val(v[r | B1]), TP::val(v[r | B0 | B1])};
+      v[r] = TP::template mac<4>(cf, x);
+      v[r | B0] = TP::template mac<4>(cf + 4, x);
+      v[r | B1] = TP::template mac<4>(cf + 8, x);
+      v[r | B0 | B1] = TP::template mac<4>(cf + 12, x);
+    }
+  }
+
+  __device__ __forceinline__ void phase(const Coef* cf, uint32_t lmask, uint32_t lpat, bool neg) {
+    const Coef c = cf[0];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r >= reff) continue;
+      if (((toff | roff(r)) & lmask) != lpat) continue;
+      if (neg) {
+        v[r] = TP::neg(v[r]);
+      } else {
+        const Val x = TP::val(v[r]);
+        v[r] = TP::template mac<1>(&c, &x);
+      }
+    }
+  }
+
+  __device__ __forceinline__ void diag(const TileOp& op, const Coef* cf, uint64_t base) {
+    uint32_t sg = 0;
+    for (int j = 0; j < op.k; ++j)
+      if (op.gq[j] != 0xFF) sg |= (uint32_t)((base >> op.gq[j]) & 1ull) << j;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r >= reff) continue;
+      const uint32_t lam = toff | roff(r);
+      if ((lam & op.lmask) != op.lmask) continue;
+      uint32_t sidx = sg;
+      for (int j = 0; j < op.nloc; ++j) sidx |= ((lam >> op.tpos[j]) & 1u) << op.tj[j];
+      const Val x = TP::val(v[r]);
+      v[r] = TP::template mac<1>(cf + sidx, &x);
+    }
+  }
+
+  // Permutation of local targets: through shared memory (write in place,
+  // read each destination's source).
+  __device__ __forceinline__ void perm(const TileOp& op, const uint8_t* inv, unsigned char* smem) {
+    consumers_sync();
+    write_sm(smem);
+    consumers_sync();
+    const Sm* t = reinterpret_cast<const Sm*>(smem);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r >= reff || !active) continue;
+      const uint32_t d = toff | roff(r);
+      uint32_t src = d;
+      if ((d & op.lmask) == op.lmask) {
+        uint32_t sidx = 0;
+        for (int j = 0; j < op.k; ++j) sidx |= ((d >> op.tpos[j]) & 1u) << j;
+        const uint32_t sv = inv[sidx];
+        for (int j = 0; j < op.k; ++j) src = (src & ~(1u << op.tpos[j])) | (((sv >> j) & 1u) << op.tpos[j]);
+      }
+      v[r] = t[src];
+    }
+  }
+};
+
+template <class RT, int K>
+__device__ __forceinline__ void dense2_k1(RT& rt, int k1, const typename RT::Coef* cf, uint32_t lmask) {
+  switch (k1) {
+    case 0: if constexpr (K != 0) rt.template dense2<K, 0>(cf, lmask); break;
+    case 1: if constexpr (K != 1) rt.template dense2<K, 1>(cf, lmask); break;
+    case 2: if constexpr (K != 2 && RT::RB > 2) rt.template dense2<K, (RT::RB > 2 ? 2 : 0)>(cf, lmask); break;
+    default: if constexpr (K != 3 && RT::RB > 3) rt.template dense2<K, (RT::RB > 3 ? 3 : 0)>(cf, lmask); break;
+  }
+}
+
+// Apply a block's ops to one tile.  ops[0] is a TOP_LAYOUT: the first read
+// converts the staged global-format tile; the tile is written back in global
+// format after the last op.
+template <class TP>
+__device__ __forceinline__ void consume_tile(unsigned char* smem, const TileOp* __restrict__ ops, int nops,
+                                             const typename TP::M::Coef* __restrict__ coefs,
+                                             const uint8_t* __restrict__ perm_tables, int tile_log, uint64_t base,
+                                             int tid) {
+  using RT = RegTile<TP>;
+  RT rt;
+  const int rb = tile_log < RT::RB ? tile_log : RT::RB;
+  bool first = true;
+  for (int o = 0; o < nops; ++o) {
+    const TileOp& op = ops[o];
+    if ((base & op.gmask) != op.gpat) continue;
+    const typename RT::Coef* cf = coefs + op.coef;
+    switch (op.kind) {
+      case TOP_LAYOUT:
+        if (first) {
+          rt.set_layout(op.tpos, rb, tile_log, tid);
+          rt.read_glob(smem);
+          first = false;
+        } else {
+          consumers_sync();
+          rt.write_sm(smem);
+          consumers_sync();
+          rt.set_layout(op.tpos, rb, tile_log, tid);
+          rt.read_sm(smem);
+        }
+        break;
+      case TOP_DENSE1:
+        switch (op.tpos[0]) {
+          case 0: rt.template dense1<0>(cf, op.lmask); break;
+          case 1: rt.template dense1<1>(cf, op.lmask); break;
+          case 2: if constexpr (RT::RB > 2) rt.template dense1<(RT::RB > 2 ? 2 : 0)>(cf, op.lmask); break;
+          default: if constexpr (RT::RB > 3) rt.template dense1<(RT::RB > 3 ? 3 : 0)>(cf, op.lmask); break;
+        }
+        break;
+      case TOP_XSWAP:
+      case TOP_Y: {
+        const bool y = op.kind == TOP_Y;
+        switch (op.tpos[0]) {
+          case 0: rt.template xswap<0>(y, op.lmask); break;
+          case 1: rt.template xswap<1>(y, op.lmask); break;
+          case 2: if constexpr (RT::RB > 2) rt.template xswap<(RT::RB > 2 ? 2 : 0)>(y, op.lmask); break;
+          default: if constexpr (RT::RB > 3) rt.template xswap<(RT::RB > 3 ? 3 : 0)>(y, op.lmask); break;
+        }
+        break;
+      }
+      case TOP_DENSE2:
+        switch (op.tpos[0]) {
+          case 0: dense2_k1<RT, 0>(rt, op.tpos[1], cf, op.lmask); break;
+          case 1: dense2_k1<RT, 1>(rt, op.tpos[1], cf, op.lmask); break;
+          case 2: if constexpr (RT::RB > 2) dense2_k1<RT, (RT::RB > 2 ? 2 : 0)>(rt, op.tpos[1], cf, op.lmask); break;
+          default: if constexpr (RT::RB > 3) dense2_k1<RT, (RT::RB > 3 ? 3 : 0)>(rt, op.tpos[1], cf, op.lmask); break;
+        }
+        break;
+      case TOP_PHASE:
+        rt.phase(cf, op.lmask, op.lpat, false);
+        break;
+      case TOP_NEG:
+        rt.phase(cf, op.lmask, op.lpat, true);
+        break;
+      case TOP_DIAG:
+        rt.diag(op, cf, base);
+        break;
+      case TOP_PERM:
+        rt.perm(op, perm_tables + op.ptab, smem);
+        break;
+    }
+  }
+  consumers_sync();
+  rt.write_glob(smem);
 }
 
 }  // namespace qs
