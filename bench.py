@@ -48,6 +48,15 @@ def parse():
     ap.add_argument("--n", type=int, default=N_QUBITS)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the fused-circuit, batched and serving measurements added to the line")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "circuits", "batch", "serve"],
+                    help="sweep: the default gate sweep; the others print one line each for the fused "
+                         "RQC/QFT circuits, the batched small states and the serving loop")
+    ap.add_argument("--count", type=int, default=4096, help="batch: number of states")
+    ap.add_argument("--nmin", type=int, default=10)
+    ap.add_argument("--nmax", type=int, default=20)
+    ap.add_argument("--requests", type=int, default=400, help="serve: number of requests")
     return ap.parse_args()
 
 
@@ -189,6 +198,157 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# Fused circuits, batched states, serving
+# ---------------------------------------------------------------------------
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def measure_circuits(qs, torch, n, fused_only=False):
+    """RQC (20 layers of sqrt-X/Y/W + brick CZ) and QFT of a random basis
+    state on n qubits, complex128 and complex64, fused (default block size)
+    and gate by gate.  Device time per circuit (CUDA events)."""
+    stream = torch.cuda.Stream()
+    x = int(W.rng_for(2510).integers(1 << n))
+    circuits = {"rqc20": W.rqc(n, 20, seed=2508), "qft": [W.X(q) for q in range(n) if (x >> q) & 1] +
+                W.qft(list(range(n)))}
+    out = {"n_qubits": n}
+    for dname, dt, e in (("c128", qs.QS_C128, 16), ("c64", qs.QS_C64, 8)):
+        st = qs.State(n, dt)
+        qs.qs_set_stream(st.h, stream.cuda_stream)
+        for label, gates in circuits.items():
+            c = qs.Circuit(gates)
+            res = {"gates": len(gates)}
+            for mode, mf in (("fused", 0), ("per_gate", 1)):
+                if fused_only and mode == "per_gate":
+                    continue
+                qs.qs_init_basis(st.h, 0)
+                st.run(c, max_fuse=mf)  # warm-up (kernel loading, plan caches)
+                qs.qs_init_basis(st.h, 0)
+                a, b = _events(torch)
+                torch.cuda.synchronize()
+                a.record(stream)
+                st.run(c, max_fuse=mf)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b)
+                res[f"{mode}_ms"] = ms
+                res[f"{mode}_gate_equiv_gbs"] = len(gates) * 2 * e * (1 << n) / (ms * 1e-3) / 1e9
+            res["norm"] = st.norm()
+            out[f"{label}_{dname}"] = res
+        st.close()
+    for label in circuits:
+        out[f"{label}_c64_speedup_vs_c128"] = out[f"{label}_c128"]["fused_ms"] / out[f"{label}_c64"]["fused_ms"]
+    return out
+
+
+def measure_batch(qs, torch, count, nmin, nmax, dtype_name="c128", seed=2512):
+    """count states, qubit counts uniform in nmin..nmax, half Grover (random
+    marked item, optimal iteration count), half Shor-like; one persistent
+    graph-captured launch.  Reports circuits/s, gates/s and effective GB/s
+    (every gate counted as one read and write of its state)."""
+    rng = W.rng_for(seed)
+    dt = qs.QS_C128 if dtype_name == "c128" else qs.QS_C64
+    e = 16 if dtype_name == "c128" else 8
+    ns = [int(v) for v in rng.integers(nmin, nmax + 1, size=count)]
+    states, circuits, n_gates, moved = [], [], 0, 0.0
+    stream = torch.cuda.Stream()
+    for i, n in enumerate(ns):
+        gates = W.grover(n, int(rng.integers(1 << n))) if i % 2 == 0 else W.shor_like(n, seed=seed * 7 + i)[0]
+        st = qs.State(n, dt)
+        qs.qs_set_stream(st.h, stream.cuda_stream)
+        states.append(st)
+        circuits.append(qs.Circuit(gates))
+        n_gates += len(gates)
+        moved += len(gates) * 2.0 * e * (1 << n)
+    handles = [s.h for s in states]
+    opts = qs.run_opts(use_graph=1)
+    t0 = time.perf_counter()
+    qs.qs_batch_run(handles, circuits, opts)  # compile + capture + first run
+    torch.cuda.synchronize()
+    compile_and_first_s = time.perf_counter() - t0
+    for st in states:
+        qs.qs_init_basis(st.h, 0)
+    a, b = _events(torch)
+    torch.cuda.synchronize()
+    a.record(stream)
+    qs.qs_batch_run(handles, circuits, opts)  # graph replay
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    for st in states:
+        st.close()
+    return {"states": count, "dtype": dtype_name, "qubits": [nmin, nmax], "gates": n_gates, "ms": ms,
+            "circuits_per_s": count / (ms * 1e-3), "gates_per_s": n_gates / (ms * 1e-3),
+            "effective_gbs": moved / (ms * 1e-3) / 1e9, "host_compile_and_first_run_s": compile_and_first_s}
+
+
+def measure_serving(qs, torch, requests, nmin, nmax, seed=2513):
+    """Closed-loop capacity (all requests at t=0), then Poisson arrivals at
+    0.7x and 1.0x that capacity; complex64 and complex128."""
+    from paper_2506_09198_gb300 import serving as S
+
+    free = torch.cuda.mem_get_info()[0]
+    out = {"requests": requests, "qubits": [nmin, nmax], "mix": "40% RQC-20 / 30% QFT / 30% Grover (r <= 16)"}
+    for dname, dt in (("c128", qs.QS_C128), ("c64", qs.QS_C64)):
+        budget = min(1 << 37, 1 << (int(free * 0.6).bit_length() - 1))
+        res = {}
+        srv = S.Server(dt, hbm_budget_bytes=budget)
+        for r in S.make_requests(requests, seed=seed, n_min=nmin, n_max=nmax, rate=0.0):
+            srv.submit(r)
+        t0 = time.perf_counter()
+        done = srv.run()
+        cap = S.summarize(done, time.perf_counter() - t0)
+        res["capacity"] = cap
+        for frac in (0.7, 1.0):
+            rate = frac * cap["circuits_per_s"]
+            srv = S.Server(dt, hbm_budget_bytes=budget)
+            for r in S.make_requests(requests, seed=seed, n_min=nmin, n_max=nmax, rate=rate):
+                srv.submit(r)
+            t0 = time.perf_counter()
+            done = srv.run()
+            summ = S.summarize(done, time.perf_counter() - t0)
+            summ["arrival_rate"] = rate
+            res[f"poisson_{frac}"] = summ
+        res["hbm_budget_bytes"] = budget
+        out[dname] = res
+        del srv
+        torch.cuda.empty_cache()
+    out["c64_vs_c128_capacity"] = out["c64"]["capacity"]["circuits_per_s"] / out["c128"]["capacity"]["circuits_per_s"]
+    return out
+
+
+def run_extra_workload(args):
+    import torch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_2506_09198_gb300 import build
+
+    build.build()
+    from paper_2506_09198_gb300 import qs
+
+    if args.workload == "circuits":
+        res = measure_circuits(qs, torch, args.n)
+        line = {"metric": "fused circuits: RQC-20 and QFT device time, complex128 vs complex64",
+                "value": res["rqc20_c64"]["fused_ms"], "unit": "ms", "higher_is_better": False,
+                "config": {"workload": f"RQC-20 and QFT on {args.n} qubits"}, "detail": res}
+    elif args.workload == "batch":
+        res = [measure_batch(qs, torch, args.count, args.nmin, args.nmax, d) for d in ("c128", "c64")]
+        line = {"metric": "batched states: circuits/s in one persistent graph-captured launch",
+                "value": res[0]["circuits_per_s"], "unit": "circuits/s", "higher_is_better": True,
+                "config": {"workload": f"{args.count} states, {args.nmin}..{args.nmax} qubits, half Grover / half "
+                                       f"Shor-like"}, "detail": res}
+    else:
+        res = measure_serving(qs, torch, args.requests, args.nmin, args.nmax)
+        line = {"metric": "served circuits/s and p99 latency, complex64 vs complex128",
+                "value": res["c128"]["capacity"]["circuits_per_s"], "unit": "circuits/s", "higher_is_better": True,
+                "config": {"workload": f"{args.requests} requests, {args.nmin}..{args.nmax} qubits log-uniform"},
+                "detail": res}
+    line["data"] = "synthetic"
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -313,6 +473,17 @@ def run_ours(args):
                          f"{secs:.1f} s single-thread"}
 
     st.close()
+    del pinned
+    extras = None
+    if rank == 0 and not args.no_extras:
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        extras = {
+            "fused_circuits": measure_circuits(qs, torch, 28),
+            "batched": measure_batch(qs, torch, 512, 10, 16, "c128"),
+            "batched_c64": measure_batch(qs, torch, 512, 10, 16, "c64"),
+            "serving": measure_serving(qs, torch, 120, 12, 24),
+        }
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -330,7 +501,8 @@ def run_ours(args):
                 "per_kernel_ms": {k: statistics.mean(v) for k, v in per_kind.items()},
                 "gbs_per_target_1q": per_target,
                 "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
-                "gpu_launches": len(gates) * args.steps}
+                "gpu_launches": len(gates) * args.steps,
+                "extras": extras}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -342,6 +514,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "sweep":
+        run_extra_workload(args)
     else:
         run_ours(args)
 

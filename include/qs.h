@@ -169,7 +169,8 @@ typedef struct {
   int32_t max_fuse;   /* fusion: 1 = none (one kernel per gate); 2..6 = most
                          qubits above the resident low block that one fused
                          block may span (the block's tile holds 2^max_fuse
-                         strided chunks); 0 = default (5) */
+                         strided chunks); 0 = the qs_autotune choice for this
+                         dtype, math mode and qubit count (3 if untuned) */
   int32_t use_graph;  /* 1: capture the launch sequence as a CUDA graph and
                          replay it (the graph is cached per circuit pointer) */
   int32_t reserved[6];
@@ -183,9 +184,25 @@ typedef struct {
  * gates one by one, up to rounding.  opts may be NULL (autotuned, no graph). */
 qs_status qs_fuse_run(qs_state s, const qs_circuit* c, const qs_run_opts* opts);
 
-/* Run circuits[i] on states[i] for i < count, all of one dtype and small
- * enough for the batched kernel (n <= 14 for complex128, 15 for complex64),
- * in one persistent launch on the first state's stream. */
+/* Autotuner for fusion: run circuit c on s with every fusion setting
+ * (max_fuse 1..6, which also sets the tile shape: 2^max_fuse strided chunks
+ * of contiguous amplitudes), time each on the device, and remember the
+ * fastest fused setting for states of s's dtype, math mode and qubit count;
+ * qs_fuse_run with max_fuse = 0 then uses it (default 3 before any tuning).
+ * s is scratch: it is reset to |0...0> before each trial and holds the last
+ * trial's result afterwards.  Synchronous.  best_max_fuse and best_ms may be
+ * NULL. */
+qs_status qs_autotune(qs_state s, const qs_circuit* c, int* best_max_fuse, double* best_ms);
+
+/* Run circuits[i] on states[i] for i < count (distinct states, one dtype and
+ * math mode), asynchronously on the first state's stream.  States of at most
+ * 16 qubits run in one persistent launch: CTAs claim whole states, largest
+ * estimated cost first, and apply each state's fused blocks in shared
+ * memory.  Wider states follow as fused whole-GPU blocks.  opts->use_graph:
+ * capture the whole sequence as a CUDA graph, cached per (states, circuits)
+ * pointer list and replayed by later calls with the same lists (the circuit
+ * contents must not change in between).  Other states' streams are
+ * synchronised before the launch. */
 qs_status qs_batch_run(qs_state* states, const qs_circuit* const* circuits, int count, const qs_run_opts* opts);
 
 /* ---- reductions (synchronous) ---------------------------------------- */

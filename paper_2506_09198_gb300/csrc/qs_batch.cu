@@ -27,6 +27,11 @@
 namespace qs {
 
 qs_status check_gate(const qs_state s, const qs_circuit* c, int64_t gi);  // qs_circuit.cu
+qs_status run_fused(qs_state s, const qs_circuit* c, int max_high);          // qs_tile.cu
+int fuse_width_for(qs_state s);                                              // qs_circuit.cu
+
+// Widest state that the persistent batched kernel runs on a single CTA.
+constexpr int kBatchLocalMax = 16;
 
 struct BatchBlock {
   int L, m, nops, pad;
@@ -67,7 +72,7 @@ __device__ __forceinline__ uint64_t chunk_offset(const BatchBlock& b, uint32_t c
 }
 
 template <class TP>
-__global__ void __launch_bounds__(kTileThreads, 2) k_batch(const BatchArgs<TP> a) {
+__global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_batch(const BatchArgs<TP> a) {
   using Glob = typename TP::Glob;
   using Sm = typename TP::Sm;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -259,7 +264,7 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
       }
       if (emitted == 0) return fail(QS_ERR_UNSUPPORTED, "batch state %d: gate %zu could not be placed", i, next);
       if (bo.ops.empty()) continue;
-      bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits);
+      bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits, TP::kBankBits);
       BatchBlock b;
       std::memset(&b, 0, sizeof(b));
       b.L = geom.L;
@@ -374,25 +379,62 @@ qs_status run_batch(qs_state* states, const qs_circuit* const* circuits, int cou
     cudaGraphExecDestroy(bc->graph);
     bc->graph = nullptr;
   }
-  qs_status st = compile_batch<TP>(states, circuits, count, bc);
-  if (st != QS_OK) return st;
+  // States up to kBatchLocalMax qubits share the persistent launch (one CTA
+  // each); wider states need the whole GPU per block and run as fused blocks
+  // after it, in the same stream order (and the same captured graph).
+  std::vector<qs_state> local_states, wide_states;
+  std::vector<const qs_circuit*> local_circuits, wide_circuits;
+  for (int i = 0; i < count; ++i) {
+    if (states[i]->n <= kBatchLocalMax) {
+      local_states.push_back(states[i]);
+      local_circuits.push_back(circuits[i]);
+    } else {
+      wide_states.push_back(states[i]);
+      wide_circuits.push_back(circuits[i]);
+    }
+  }
+  qs_status st = QS_OK;
+  if (!local_states.empty()) {
+    st = compile_batch<TP>(local_states.data(), local_circuits.data(), (int)local_states.size(), bc);
+    if (st != QS_OK) return st;
+  } else {
+    bc->n_states = 0;
+  }
   bc->key = key;
   bc->dtype = (int)s0->dtype;
   bc->math = (int)s0->math;
   // Every state's pending work must finish before the batch touches it.
   for (int i = 1; i < count; ++i)
     if (states[i]->stream != s0->stream) QS_CUDA(cudaStreamSynchronize(states[i]->stream));
-  if (!use_graph) return launch_batch<TP>(s0, bc, s0->stream);
+  auto enqueue = [&](cudaStream_t stream) -> qs_status {
+    if (bc->n_states > 0) {
+      qs_status r = launch_batch<TP>(s0, bc, stream);
+      if (r != QS_OK) return r;
+    }
+    for (size_t i = 0; i < wide_states.size(); ++i) {
+      qs_state w = wide_states[i];
+      cudaStream_t saved = w->stream;
+      w->stream = stream;
+      qs_status r = run_fused(w, wide_circuits[i], fuse_width_for(w));
+      w->stream = saved;
+      if (r != QS_OK) return r;
+    }
+    return QS_OK;
+  };
+  if (!use_graph) return enqueue(s0->stream);
   cudaStream_t cap;
   QS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    st = launch_batch<TP>(s0, bc, cap);
+    st = enqueue(cap);
     e = cudaStreamEndCapture(cap, &g);
   }
   cudaStreamDestroy(cap);
-  if (st != QS_OK) return st;
+  if (st != QS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
   if (e != cudaSuccess) return cuda_fail(e, "batch graph capture");
   e = cudaGraphInstantiate(&bc->graph, g, 0);
   cudaGraphDestroy(g);

@@ -1,5 +1,8 @@
 // Circuit runner: validation of qs_circuit records and gate-by-gate dispatch.
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "qs_internal.h"
@@ -12,6 +15,21 @@ qs_status batch_run(qs_state* states, const qs_circuit* const* circuits, int cou
 void release_batch_cache(qs_state s);           // qs_batch.cu
 
 void release_plan_cache(qs_state s) { release_batch_cache(s); }
+
+// Fusion width chosen by qs_autotune, per (device, dtype, math, qubits).
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int>, int> g_tuned;
+constexpr int kDefaultMaxFuse = 3;
+
+int fuse_width_for(qs_state s);
+
+static int tuned_max_fuse(qs_state s) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find(std::make_tuple(s->device, (int)s->dtype, (int)s->math, s->n));
+  return it == g_tuned.end() ? kDefaultMaxFuse : it->second;
+}
+
+int fuse_width_for(qs_state s) { return tuned_max_fuse(s); }
 
 // Validates one gate record against the state and returns its control mask.
 qs_status check_gate(const qs_state s, const qs_circuit* c, int64_t gi) {
@@ -77,6 +95,16 @@ qs_status check_gate(const qs_state s, const qs_circuit* c, int64_t gi) {
   return QS_OK;
 }
 
+qs_status apply_gate_record(qs_state s, const qs_circuit* c, const qs_gate& g);
+
+qs_status qs_fuse_run_gatewise(qs_state s, const qs_circuit* c) {
+  for (int64_t i = 0; i < c->n_gates; ++i) {
+    qs_status st = apply_gate_record(s, c, c->gates[i]);
+    if (st != QS_OK) return st;
+  }
+  return QS_OK;
+}
+
 qs_status apply_gate_record(qs_state s, const qs_circuit* c, const qs_gate& g) {
   switch (g.kind) {
     case QS_GATE_U1:
@@ -107,12 +135,55 @@ qs_status qs_fuse_run(qs_state s, const qs_circuit* c, const qs_run_opts* opts) 
     if (st != QS_OK) return st;
   }
   if (c->n_gates == 0) return QS_OK;
-  if (max_fuse != 1) return run_fused(s, c, max_fuse == 0 ? 5 : max_fuse);
+  if (max_fuse != 1) return run_fused(s, c, max_fuse == 0 ? tuned_max_fuse(s) : max_fuse);
+  return qs_fuse_run_gatewise(s, c);
+}
+
+qs_status qs_autotune(qs_state s, const qs_circuit* c, int* best_max_fuse, double* best_ms) {
+  if (!s) return fail(QS_ERR_ARG, "state handle is NULL");
+  if (!c || c->n_gates < 0 || (c->n_gates > 0 && !c->gates)) return fail(QS_ERR_ARG, "bad circuit");
   for (int64_t i = 0; i < c->n_gates; ++i) {
-    qs_status st = apply_gate_record(s, c, c->gates[i]);
+    qs_status st = check_gate(s, c, i);
     if (st != QS_OK) return st;
   }
-  return QS_OK;
+  cudaEvent_t a, b;
+  QS_CUDA(cudaEventCreate(&a));
+  QS_CUDA(cudaEventCreate(&b));
+  int best = 1;
+  float best_t = 0.f;
+  qs_status st = QS_OK;
+  for (int mf = 1; mf <= 6 && st == QS_OK; ++mf) {
+    // one untimed run (kernel loading), one timed
+    for (int rep = 0; rep < 2 && st == QS_OK; ++rep) {
+      st = launch_init_basis(s, 0);
+      if (st != QS_OK) break;
+      if (rep == 1 && cudaEventRecord(a, s->stream) != cudaSuccess) st = fail(QS_ERR_CUDA, "event record");
+      if (st == QS_OK) st = mf == 1 ? qs_fuse_run_gatewise(s, c) : run_fused(s, c, mf);
+      if (st == QS_OK && rep == 1 && cudaEventRecord(b, s->stream) != cudaSuccess) st = fail(QS_ERR_CUDA, "event record");
+    }
+    if (st != QS_OK) break;
+    if (cudaEventSynchronize(b) != cudaSuccess) {
+      st = fail(QS_ERR_CUDA, "event synchronize");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (mf == 1 || ms < best_t) {
+      best = mf;
+      best_t = ms;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (st != QS_OK) return st;
+  if (best == 1) best = 2;  // max_fuse = 0 always fuses; keep the narrowest block if gate-by-gate won
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[std::make_tuple(s->device, (int)s->dtype, (int)s->math, s->n)] = best;
+  }
+  if (best_max_fuse) *best_max_fuse = best;
+  if (best_ms) *best_ms = best_t;
+  return device_error_check(s);
 }
 
 qs_status qs_batch_run(qs_state* states, const qs_circuit* const* circuits, int count, const qs_run_opts* opts) {

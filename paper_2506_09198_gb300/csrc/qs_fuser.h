@@ -325,31 +325,24 @@ inline uint32_t reg_need(const TileOp& op) {
 // registers, and rewrite those targets as register bit indices.  A new layout
 // takes the targets of the op that needs it plus those of the following ops,
 // in order, while they fit in rb register bits; free register slots take the
-// highest remaining local bits (the low bits stay thread bits, so shared
-// memory accesses of a warp fall on consecutive amplitudes).
-inline std::vector<TileOp> schedule_layouts(const std::vector<TileOp>& ops, int tile_log, int reg_bits) {
+// highest remaining local bits.
+//
+// The staged tile sits in shared memory in plain order, so the first read and
+// the last write are free of bank conflicts only when the lowest `bank_bits`
+// local bits are thread bits (lanes then touch consecutive amplitudes).  If
+// the first layout needs one of those bits in registers, the tile is read in
+// a bank-friendly layout first and transposed (layout changes go through a
+// swizzled arrangement); likewise before the final write.
+inline std::vector<TileOp> schedule_layouts(const std::vector<TileOp>& ops, int tile_log, int reg_bits,
+                                            int bank_bits) {
   const int rb = tile_log < reg_bits ? tile_log : reg_bits;
+  const uint32_t low = tile_log > bank_bits + rb ? ((1u << bank_bits) - 1u) : 0u;
   std::vector<TileOp> out;
   out.reserve(ops.size() + 8);
   uint32_t cur = 0;
   int pos_of[32];
   bool have = false;
-  auto make_layout = [&](size_t i) {
-    uint32_t set = 0;
-    int cnt = 0;
-    for (size_t j = i; j < ops.size(); ++j) {
-      const uint32_t need = reg_need(ops[j]);
-      if (!need) continue;
-      const uint32_t u = set | need;
-      if (__builtin_popcount(u) > rb) break;
-      set = u;
-      cnt = __builtin_popcount(set);
-    }
-    for (int b = tile_log - 1; b >= 0 && cnt < rb; --b)
-      if (!((set >> b) & 1u)) {
-        set |= 1u << b;
-        ++cnt;
-      }
+  auto emit = [&](uint32_t set) {
     TileOp lay;
     std::memset(&lay, 0, sizeof(lay));
     lay.kind = TOP_LAYOUT;
@@ -365,6 +358,28 @@ inline std::vector<TileOp> schedule_layouts(const std::vector<TileOp>& ops, int 
     have = true;
     out.push_back(lay);
   };
+  auto fill_high = [&](uint32_t set) {
+    int cnt = __builtin_popcount(set);
+    for (int b = tile_log - 1; b >= 0 && cnt < rb; --b)
+      if (!((set >> b) & 1u)) {
+        set |= 1u << b;
+        ++cnt;
+      }
+    return set;
+  };
+  auto make_layout = [&](size_t i) {
+    uint32_t set = 0;
+    for (size_t j = i; j < ops.size(); ++j) {
+      const uint32_t need = reg_need(ops[j]);
+      if (!need) continue;
+      const uint32_t u = set | need;
+      if (__builtin_popcount(u) > rb) break;
+      set = u;
+    }
+    set = fill_high(set);
+    if (!have && (set & low)) emit(fill_high(0));  // bank-friendly first read
+    emit(set);
+  };
   for (size_t i = 0; i < ops.size(); ++i) {
     const uint32_t need = reg_need(ops[i]);
     if (!have || (need & ~cur)) make_layout(i);
@@ -376,6 +391,7 @@ inline std::vector<TileOp> schedule_layouts(const std::vector<TileOp>& ops, int 
     out.push_back(op);
   }
   if (!have) make_layout(0);
+  if (cur & low) emit(fill_high(0));  // bank-friendly last write
   return out;
 }
 

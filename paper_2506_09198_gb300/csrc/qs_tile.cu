@@ -33,7 +33,7 @@
 namespace qs {
 
 template <class TP>
-__global__ void __launch_bounds__(kTileThreads, 2) k_tile(typename TP::Glob* __restrict__ psi,
+__global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_tile(typename TP::Glob* __restrict__ psi,
                                                        const __grid_constant__ TilePlan<typename TP::M::Coef> plan,
                                                        uint32_t* __restrict__ err) {
   using Glob = typename TP::Glob;
@@ -169,16 +169,24 @@ qs_status launch_plan(qs_state s, const TilePlan<typename TP::M::Coef>& plan) {
   const size_t tile_bytes = sizeof(typename TP::Glob) << (plan.L + plan.m);
   const size_t smem = kStages * tile_bytes + 2 * kStages * sizeof(uint64_t);
   auto kern = k_tile<TP>;
+  // The dynamic shared-memory limit is a property of the function: set it
+  // once to the largest tile so that launches with any tile size are valid.
   static std::mutex mu;
+  static bool attr_set = false;
   static std::unordered_map<int, int> occ_cache;
   int occ = 0;
   {
     std::lock_guard<std::mutex> lk(mu);
+    if (!attr_set) {
+      const size_t max_smem =
+          kStages * ((size_t)sizeof(typename TP::Glob) << TP::kTileLog) + 2 * kStages * sizeof(uint64_t);
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_tile)");
+      attr_set = true;
+    }
     const int key = (int)smem;
     auto it = occ_cache.find(key);
     if (it == occ_cache.end()) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_tile)");
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTileThreads, smem) != cudaSuccess || occ < 1)
         occ = 1;
       occ_cache[key] = occ;
@@ -192,7 +200,9 @@ qs_status launch_plan(qs_state s, const TilePlan<typename TP::M::Coef>& plan) {
   if (!err) return fail(QS_ERR_CUDA, "device error word unavailable");
   kern<<<grid, kTileThreads, smem, s->stream>>>((typename TP::Glob*)s->psi, plan, err);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "k_tile");
+  if (e != cudaSuccess)
+    return fail(QS_ERR_CUDA, "k_tile launch (grid %u, smem %zu, plan %zu bytes, %d ops, L %d, m %d): %s", grid, smem,
+                sizeof(plan), plan.nops, plan.L, plan.m, cudaGetErrorString(e));
   return QS_OK;
 }
 
@@ -208,8 +218,9 @@ qs_status run_blocks(qs_state s, const std::vector<FGate>& gates, int max_high) 
   using Coef = typename TP::M::Coef;
   const int n = s->n;
   const int min_chunk = sizeof(typename TP::Glob) == 16 ? kMinChunkLog128 : kMinChunkLog64;
-  // Scheduling adds at most one layout change per gate.
-  const Limits lim{kTileMaxOps / 2, kTileMaxCoefs, kTileMaxPermBytes};
+  // Scheduling adds at most one layout change per gate, plus one before the
+  // first and one after the last.
+  const Limits lim{kTileMaxOps / 2 - 1, kTileMaxCoefs, kTileMaxPermBytes};
   static thread_local std::vector<unsigned char> plan_mem;
   plan_mem.resize(sizeof(TilePlan<Coef>));
   TilePlan<Coef>* plan = reinterpret_cast<TilePlan<Coef>*>(plan_mem.data());
@@ -246,7 +257,7 @@ qs_status run_blocks(qs_state s, const std::vector<FGate>& gates, int max_high) 
       continue;
     }
     if (!bo.ops.empty()) {
-      bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits);
+      bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits, TP::kBankBits);
       fill_plan(plan, n, bo);
       qs_status st = launch_plan<TP>(s, *plan);
       if (st != QS_OK) return st;

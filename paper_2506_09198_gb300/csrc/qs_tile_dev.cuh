@@ -12,9 +12,16 @@
 
 namespace qs {
 
+#ifndef QS_TILE_STAGES
+#define QS_TILE_STAGES 3
+#endif
+#ifndef QS_TILE_MIN_CTAS
+#define QS_TILE_MIN_CTAS 2
+#endif
 constexpr int kTileConsumers = 256;
 constexpr int kTileThreads = kTileConsumers + 32;
-constexpr int kStages = 3;
+constexpr int kStages = QS_TILE_STAGES;
+constexpr int kTileMinCtas = QS_TILE_MIN_CTAS;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 // ---------------------------------------------------------------------------
@@ -98,6 +105,7 @@ struct TileF32 {
   using Sm = float2;
   static constexpr int kTileLog = 12;  // 4096 amplitudes, 32 KB
   static constexpr int kRegBits = 4;  // 16 amplitudes per thread
+  static constexpr int kBankBits = 4;  // 16 amplitudes per 128-byte shared-memory row
   static __device__ __forceinline__ Sm to_sm(Glob g) { return g; }
   static __device__ __forceinline__ Glob from_sm(Sm s) { return s; }
   static __device__ __forceinline__ M::Val val(Sm s) { return M::load(s); }
@@ -122,6 +130,7 @@ struct TileF64 {
   using Sm = double2;
   static constexpr int kTileLog = 11;  // 2048 amplitudes, 32 KB
   static constexpr int kRegBits = 3;  // 8 amplitudes per thread
+  static constexpr int kBankBits = 3;  // 8 amplitudes per 128-byte shared-memory row
   static __device__ __forceinline__ Sm to_sm(Glob g) { return g; }
   static __device__ __forceinline__ Glob from_sm(Sm s) { return s; }
   static __device__ __forceinline__ M::Val val(Sm s) { return M::load(s); }
@@ -139,6 +148,7 @@ struct TileDF {
   using Sm = float4;
   static constexpr int kTileLog = 11;
   static constexpr int kRegBits = 3;  // 8 amplitudes per thread
+  static constexpr int kBankBits = 3;  // 8 amplitudes per 128-byte shared-memory row
   static __device__ __forceinline__ Sm to_sm(Glob g) {
     Sm s;
     d2ff(g.x, s.x, s.z);
@@ -160,10 +170,11 @@ struct TileDF {
   template <int K>
   static __device__ __forceinline__ Sm mac(const M::Coef* c, const M::Val* v) {
     const DF2Acc a = M::mac<K>(c, v);
-    // TwoSum(S, C) -> normalised head and tail
+    // Renormalise (S, C) to head and tail with Fast2Sum (Dekker 1971); C is
+    // the lower-order part, so the head absorbs it and the tail keeps the
+    // remainder.
     const float2 s = add2(a.S, a.C);
-    const float2 bb = sub2(s, a.S);
-    const float2 e = add2(sub2(a.S, sub2(s, bb)), sub2(a.C, bb));
+    const float2 e = sub2(a.C, sub2(s, a.S));
     return make_float4(s.x, s.y, e.x, e.y);
   }
   static __device__ __forceinline__ float fneg(float x) { return __uint_as_float(__float_as_uint(x) ^ 0x80000000u); }
@@ -195,8 +206,19 @@ struct RegTile {
   Sm v[R];
   uint32_t pbit[RB];  // local index bit of register bit j (0 when unused)
   uint32_t toff;      // local index bits of this thread
-  int reff;           // registers in use (fewer for tiles smaller than 2^RB)
+  int reff;           // registers in use (SMALL: tiles smaller than 2^RB)
   bool active;        // this thread holds amplitudes
+
+  // Shared-memory position of local index lam for layout changes: within
+  // each 128-byte row the column is XORed with the row number, so a warp
+  // whose lanes differ only in high local bits still spreads over all banks.
+  static constexpr int kSwB = sizeof(typename TP::Sm) == 16 ? 3 : 4;
+  static __device__ __forceinline__ uint32_t swz(uint32_t lam) {
+    return lam ^ ((lam >> kSwB) & ((1u << kSwB) - 1u));
+  }
+  // Registers beyond 2^tile_log (tiles smaller than 2^RB amplitudes) carry
+  // no amplitude: ops may compute on them, reads and writes skip them.
+  __device__ __forceinline__ bool live(int r) const { return r < reff; }
 
   // Local index bits of register r (r is a compile-time constant in the
   // unrolled loops, so this folds to a few ORs).
@@ -233,28 +255,28 @@ struct RegTile {
     const Glob* g = reinterpret_cast<const Glob*>(smem);
 #pragma unroll
     for (int r = 0; r < R; ++r)
-      if (r < reff && active) v[r] = TP::to_sm(g[toff | roff(r)]);
+      if (live(r) && active) v[r] = TP::to_sm(g[toff | roff(r)]);
   }
   __device__ __forceinline__ void read_sm(const unsigned char* smem) {
     const Sm* t = reinterpret_cast<const Sm*>(smem);
 #pragma unroll
     for (int r = 0; r < R; ++r)
-      if (r < reff && active) v[r] = t[toff | roff(r)];
+      if (live(r) && active) v[r] = t[swz(toff | roff(r))];
   }
   __device__ __forceinline__ void write_sm(unsigned char* smem) const {
     Sm* t = reinterpret_cast<Sm*>(smem);
 #pragma unroll
     for (int r = 0; r < R; ++r)
-      if (r < reff && active) t[toff | roff(r)] = v[r];
+      if (live(r) && active) t[swz(toff | roff(r))] = v[r];
   }
   __device__ __forceinline__ void write_glob(unsigned char* smem) const {
     Glob* g = reinterpret_cast<Glob*>(smem);
 #pragma unroll
     for (int r = 0; r < R; ++r)
-      if (r < reff && active) g[toff | roff(r)] = TP::from_sm(v[r]);
+      if (live(r) && active) g[toff | roff(r)] = TP::from_sm(v[r]);
   }
 
-  template <int K>
+  template <int K, bool CTRL>
   __device__ __forceinline__ void dense1(const Coef* cf, uint32_t lmask) {
     Coef c[4];
 #pragma unroll
@@ -262,8 +284,7 @@ struct RegTile {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (r & (1 << K)) continue;
-      if (r >= reff) continue;
-      if (((toff | roff(r)) & lmask) != lmask) continue;
+      if (CTRL && ((toff | roff(r)) & lmask) != lmask) continue;
       const Val x[2] = {TP::val(v[r]), TP::val(v[r | (1 << K)])};
       v[r] = TP::template mac<2>(c, x);
       v[r | (1 << K)] = TP::template mac<2>(c + 2, x);
@@ -275,7 +296,6 @@ struct RegTile {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (r & (1 << K)) continue;
-      if (r >= reff) continue;
       if (((toff | roff(r)) & lmask) != lmask) continue;
       const Sm a = v[r], b = v[r | (1 << K)];
       v[r] = y ? TP::mul_minus_i(b) : b;
@@ -289,8 +309,7 @@ struct RegTile {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (r & (B0 | B1)) continue;
-      if (r >= reff) continue;
-      if (((toff | roff(r)) & lmask) != lmask) continue;
+      if (lmask && ((toff | roff(r)) & lmask) != lmask) continue;
       const Val x[4] = {TP::val(v[r]), TP::val(v[r | B0]), TP::val(v[r | B1]), TP::val(v[r | B0 | B1])};
       v[r] = TP::template mac<4>(cf, x);
       v[r | B0] = TP::template mac<4>(cf + 4, x);
@@ -303,7 +322,6 @@ struct RegTile {
     const Coef c = cf[0];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      if (r >= reff) continue;
       if (((toff | roff(r)) & lmask) != lpat) continue;
       if (neg) {
         v[r] = TP::neg(v[r]);
@@ -320,7 +338,6 @@ struct RegTile {
       if (op.gq[j] != 0xFF) sg |= (uint32_t)((base >> op.gq[j]) & 1ull) << j;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      if (r >= reff) continue;
       const uint32_t lam = toff | roff(r);
       if ((lam & op.lmask) != op.lmask) continue;
       uint32_t sidx = sg;
@@ -339,7 +356,7 @@ struct RegTile {
     const Sm* t = reinterpret_cast<const Sm*>(smem);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      if (r >= reff || !active) continue;
+      if (!live(r) || !active) continue;
       const uint32_t d = toff | roff(r);
       uint32_t src = d;
       if ((d & op.lmask) == op.lmask) {
@@ -348,7 +365,7 @@ struct RegTile {
         const uint32_t sv = inv[sidx];
         for (int j = 0; j < op.k; ++j) src = (src & ~(1u << op.tpos[j])) | (((sv >> j) & 1u) << op.tpos[j]);
       }
-      v[r] = t[src];
+      v[r] = t[swz(src)];
     }
   }
 };
@@ -378,6 +395,7 @@ __device__ __forceinline__ void consume_tile(unsigned char* smem, const TileOp* 
   for (int o = 0; o < nops; ++o) {
     const TileOp& op = ops[o];
     if ((base & op.gmask) != op.gpat) continue;
+    if (!rt.active && op.kind != TOP_LAYOUT && op.kind != TOP_PERM) continue;
     const typename RT::Coef* cf = coefs + op.coef;
     switch (op.kind) {
       case TOP_LAYOUT:
@@ -394,11 +412,20 @@ __device__ __forceinline__ void consume_tile(unsigned char* smem, const TileOp* 
         }
         break;
       case TOP_DENSE1:
-        switch (op.tpos[0]) {
-          case 0: rt.template dense1<0>(cf, op.lmask); break;
-          case 1: rt.template dense1<1>(cf, op.lmask); break;
-          case 2: if constexpr (RT::RB > 2) rt.template dense1<(RT::RB > 2 ? 2 : 0)>(cf, op.lmask); break;
-          default: if constexpr (RT::RB > 3) rt.template dense1<(RT::RB > 3 ? 3 : 0)>(cf, op.lmask); break;
+        if (op.lmask == 0) {
+          switch (op.tpos[0]) {
+            case 0: rt.template dense1<0, false>(cf, 0); break;
+            case 1: rt.template dense1<1, false>(cf, 0); break;
+            case 2: if constexpr (RT::RB > 2) rt.template dense1<(RT::RB > 2 ? 2 : 0), false>(cf, 0); break;
+            default: if constexpr (RT::RB > 3) rt.template dense1<(RT::RB > 3 ? 3 : 0), false>(cf, 0); break;
+          }
+        } else {
+          switch (op.tpos[0]) {
+            case 0: rt.template dense1<0, true>(cf, op.lmask); break;
+            case 1: rt.template dense1<1, true>(cf, op.lmask); break;
+            case 2: if constexpr (RT::RB > 2) rt.template dense1<(RT::RB > 2 ? 2 : 0), true>(cf, op.lmask); break;
+            default: if constexpr (RT::RB > 3) rt.template dense1<(RT::RB > 3 ? 3 : 0), true>(cf, op.lmask); break;
+          }
         }
         break;
       case TOP_XSWAP:

@@ -80,6 +80,7 @@ _SIGS = {
     "qs_probs": [_P, _PI, _I, _PD],
     "qs_sync": [_P, ctypes.c_double],
     "qs_probs_noalloc": [_P, _I, _I, _PI, _I, _P, _P],
+    "qs_autotune": [_P, ctypes.POINTER(qs_circuit), _PI, _PD],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -284,6 +285,15 @@ def run_opts(max_fuse: int = 0, use_graph: int = 0):
 
 def qs_fuse_run(h, circuit: Circuit, opts: qs_run_opts | None = None):
     _check(_lib.qs_fuse_run(h, circuit.ptr, ctypes.byref(opts) if opts is not None else None))
+
+
+def qs_autotune(h, circuit: Circuit):
+    """Time every fusion setting of circuit on the scratch state h; returns
+    (best max_fuse, its device time in ms)."""
+    best = ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(_lib.qs_autotune(h, circuit.ptr, ctypes.byref(best), ctypes.byref(ms)))
+    return best.value, ms.value
 
 
 def qs_batch_run(handles, circuits, opts: qs_run_opts | None = None):

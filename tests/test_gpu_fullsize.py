@@ -1,0 +1,187 @@
+"""Parity at the full workload sizes, on sampled outputs the oracle computes
+one by one, or through properties that hold at any size.
+
+- 30-qubit complex128 gate sweep (16 GiB, the benchmark's launch
+  configuration): each checked gate starts from the pristine seeded state
+  (a device copy restored before the gate); sampled outputs are compared with
+  the oracle applied to the 2- or 4-amplitude sub-state they depend on.
+- 32-qubit QFT of a random basis state (complex128 64 GiB, complex64 32 GiB):
+  sampled amplitudes against the closed form.
+- 32-qubit RQC (20 layers): norm, and complex64 vs complex128 fidelity.
+- 24-qubit RQC: full state against the oracle.
+- Batched states of 10..20 qubits: Grover success probability and the
+  Shor-like counting distribution.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_common import C128_TOL, qs
+from pins import qft_closed_form, shor_counting_distribution
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2506_09198_gb300 import build
+
+    build.build()
+    O.build()
+
+
+def _sample_indices(n, count, seed):
+    rng = W.rng_for(seed)
+    idx = rng.integers(0, 1 << n, size=count, dtype=np.uint64)
+    edges = np.array([0, 1, (1 << n) - 1, (1 << (n - 1)), (1 << (n - 1)) - 1], dtype=np.uint64)
+    return np.unique(np.concatenate([idx, edges]))
+
+
+def test_sweep_30q_c128_sampled():
+    torch = pytest.importorskip("torch")
+    q = qs()
+    n = 30
+    psi = W.random_state(n, 2507)  # the benchmark's state
+    pristine = torch.from_numpy(psi.view(np.float64)).cuda()
+    work = torch.empty_like(pristine)
+    stream = torch.cuda.current_stream().cuda_stream
+    h = q.qs_wrap(n, q.QS_C128, work.data_ptr(), stream)
+    g1s, g2s = W.gate_sweep(n, 64, seed=2507)  # the benchmark's gates
+    idx = _sample_indices(n, 4096, seed=11)
+    out = np.empty(idx.size, dtype=np.complex128)
+    checked = [g1s[t] for t in (0, 1, 2, 4, 5, 9, 17, 28, 29)] + g2s[:6]
+    for g in checked:
+        work.copy_(pristine)
+        q.qs_apply_1q(h, g.targets[0], g.data) if g.kind == "u1" else \
+            q.qs_apply_2q(h, g.targets[0], g.targets[1], g.data)
+        q.qs_gather(h, idx, out)
+        i64 = idx.astype(np.int64)
+        if g.kind == "u1":
+            t = g.targets[0]
+            up = i64 & ~(1 << t)
+            sub = np.stack([psi[up], psi[up | (1 << t)]], axis=1)
+            want = np.empty(idx.size, dtype=np.complex128)
+            for j in range(idx.size):
+                res = O.apply_1q(sub[j].copy(), 0, g.data)
+                want[j] = res[(i64[j] >> t) & 1]
+        else:
+            t0, t1 = g.targets
+            base = i64 & ~((1 << t0) | (1 << t1))
+            quads = np.stack([psi[base], psi[base | (1 << t0)], psi[base | (1 << t1)],
+                              psi[base | (1 << t0) | (1 << t1)]], axis=1)
+            want = np.empty(idx.size, dtype=np.complex128)
+            for j in range(idx.size):
+                res = O.apply_kq(quads[j].copy(), [0, 1], g.data)
+                want[j] = res[((i64[j] >> t0) & 1) + 2 * ((i64[j] >> t1) & 1)]
+        err = float(np.max(np.abs(out - want)))
+        assert err <= C128_TOL, f"gate {g.kind} {g.targets}: max error {err:.3e}"
+    q.qs_destroy(h)
+
+
+@pytest.mark.parametrize("dtype_name", ["c128", "c64"])
+def test_qft_32q_closed_form_sampled(dtype_name):
+    q = qs()
+    n = 32
+    dt = q.QS_C128 if dtype_name == "c128" else q.QS_C64
+    x = int(W.rng_for(2510).integers(1 << n))
+    st = q.State(n, dt)
+    q.qs_init_basis(st.h, x)
+    st.run(W.qft(list(range(n))))
+    idx = _sample_indices(n, 1 << 14, seed=12)
+    got = st.gather(idx).astype(np.complex128)
+    want = qft_closed_form(n, x, idx.astype(np.int64))
+    err = float(np.max(np.abs(got - want)))
+    # complex128: 1e-12; complex64 amplitudes are 2^-16 in size, FP32 gives ~1e-11
+    tol = C128_TOL if dtype_name == "c128" else 1e-9
+    assert err <= tol, f"QFT 32q {dtype_name}: max error {err:.3e}"
+    assert abs(st.norm() - 1.0) < (1e-12 if dtype_name == "c128" else 1e-4)
+    st.close()
+
+
+def test_rqc_32q_norm_and_c64_fidelity():
+    torch = pytest.importorskip("torch")
+    q = qs()
+    n = 32
+    gates = W.rqc(n, 20, seed=2508)
+    a = torch.zeros(1 << n, dtype=torch.complex128, device="cuda")
+    b = torch.zeros(1 << n, dtype=torch.complex64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    ha = q.qs_wrap(n, q.QS_C128, a.data_ptr(), stream)
+    hb = q.qs_wrap(n, q.QS_C64, b.data_ptr(), stream)
+    q.qs_init_basis(ha, 0)
+    q.qs_init_basis(hb, 0)
+    c = q.Circuit(gates)
+    q.qs_fuse_run(ha, c)
+    q.qs_fuse_run(hb, c)
+    assert abs(q.qs_norm(ha) - 1.0) < 1e-12
+    # fidelity |<b|a>|^2 / (|a|^2 |b|^2), accumulated in FP64 chunk by chunk
+    inner = 0j
+    na = nb = 0.0
+    chunk = 1 << 26
+    for lo in range(0, 1 << n, chunk):
+        xa = a[lo:lo + chunk]
+        xb = b[lo:lo + chunk].to(torch.complex128)
+        inner += complex(torch.vdot(xb, xa).item())
+        na += float(torch.vdot(xa, xa).real.item())
+        nb += float(torch.vdot(xb, xb).real.item())
+    fid = abs(inner) ** 2 / (na * nb)
+    assert fid >= 1 - 1e-5, f"fidelity {fid}"
+    q.qs_destroy(ha)
+    q.qs_destroy(hb)
+
+
+@pytest.mark.parametrize("dtype_name", ["c128_df", "c64"])
+def test_rqc_24q_full_state(dtype_name):
+    q = qs()
+    n = 24
+    gates = W.rqc(n, 20, seed=2508)
+    ref = O.run_circuit(O.basis_state(n), gates)
+    dt = q.QS_C128 if dtype_name == "c128_df" else q.QS_C64
+    st = q.State(n, dt)
+    st.run(gates)
+    got = st.read().astype(np.complex128)
+    st.close()
+    if dtype_name == "c128_df":
+        assert float(np.max(np.abs(got - ref))) <= C128_TOL
+    else:
+        fid = abs(np.vdot(got, ref)) ** 2 / (np.vdot(got, got).real * np.vdot(ref, ref).real)
+        assert fid >= 1 - 1e-5
+
+
+@pytest.mark.parametrize("dtype_name", ["c128", "c64"])
+def test_batched_10_to_20_qubits(dtype_name):
+    """Grover (random marked item, optimal iterations) and Shor-like states of
+    every size 10..20, one batched launch."""
+    q = qs()
+    dt = q.QS_C128 if dtype_name == "c128" else q.QS_C64
+    rng = W.rng_for(2511)
+    states, circuits, meta = [], [], []
+    for n in range(10, 21):
+        marked = int(rng.integers(1 << n))
+        states.append(q.State(n, dt))
+        circuits.append(q.Circuit(W.grover(n, marked)))
+        meta.append(("grover", n, marked))
+        gates, prm = W.shor_like(n, seed=2600 + n)
+        states.append(q.State(n, dt))
+        circuits.append(q.Circuit(gates))
+        meta.append(("shor", n, prm))
+    q.qs_batch_run([s.h for s in states], circuits)
+    for st, m in zip(states, meta):
+        if m[0] == "grover":
+            _, n, marked = m
+            r = W.grover_iterations(n)
+            theta = math.asin(2.0 ** (-n / 2))
+            amp = st.gather([marked])[0]
+            want = math.sin((2 * r + 1) * theta) ** 2
+            tol = 1e-9 if dtype_name == "c128" else 5e-3
+            assert abs(abs(amp) ** 2 - want) < tol, f"Grover n={n}"
+        else:
+            _, n, prm = m
+            got = st.probs(list(range(prm["t"])))
+            want = shor_counting_distribution(prm["t"], prm["a"], prm["N"])
+            tol = 1e-10 if dtype_name == "c128" else 1e-4
+            assert np.max(np.abs(got - want)) < tol, f"Shor-like n={n}"
+        st.close()
