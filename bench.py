@@ -35,6 +35,11 @@ N_PAIRS = 64
 SEED_STATE = 2507
 SEED_GATES = 2507
 WORKLOAD = "gate sweep, 30-qubit complex128 state (16 GiB): Haar 1q on targets 0..29 + Haar 2q on 64 random pairs"
+# DRAM bytes (read + write) per launch from one ncu capture at 26 qubits, scaled
+# to 30 qubits by the amplitude count (profiles/k_dense_df_26q_c128.md).  Valid
+# for the float-float kernels as profiled; other variants report null.
+NCU_TRAFFIC_30Q = {("k_dense2", "c128", "df"): (1.073815e9 + 1.012505e9) * 16,
+                   ("k_dense1", "c128", "df"): (1.073995e9 + 1.012920e9) * 16}
 
 
 def parse():
@@ -496,8 +501,9 @@ def run_ours(args):
                            "gates_per_step": len(gates), "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (16 GiB state, 129 MB L2)"},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": None, "kernel": dom,
-                             "peak_source": peak_src},
+                             "frac": achieved / peak,
+                             "traffic": NCU_TRAFFIC_30Q.get((dom, args.dtype, args.math)) if n == 30 else None,
+                             "kernel": dom, "peak_source": peak_src},
                 "per_kernel_ms": {k: statistics.mean(v) for k, v in per_kind.items()},
                 "gbs_per_target_1q": per_target,
                 "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
