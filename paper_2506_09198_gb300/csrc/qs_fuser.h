@@ -9,6 +9,7 @@
 // runner (qs_tile.cu) and by the batched kernel (qs_batch.cu).
 #pragma once
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <functional>
 #include <vector>
@@ -20,6 +21,22 @@ namespace qs {
 namespace fuser {
 
 inline bool is_c(const double* z, double re, double im) { return z[0] == re && z[1] == im; }
+
+// Smallest e with sum_c (|re u_rc| + |im u_rc|) (entries rounded to float)
+// < 2^e, stored biased by 128: the anchored float-float accumulation of
+// dense rows needs this bound.
+inline uint8_t row_exp_biased(const double* U, int row, int dim) {
+  double sum = 0.0;
+  for (int c = 0; c < dim; ++c) {
+    const double* z = U + 2 * (row * dim + c);
+    sum += std::fabs((double)(float)z[0]) + std::fabs((double)(float)z[1]);
+  }
+  int e = -126;
+  if (sum > 0.0) std::frexp(sum, &e);
+  if (e < -126) e = -126;
+  if (e > 127) e = 127;
+  return (uint8_t)(e + 128);
+}
 
 // One gate record in normalised form.
 struct FGate {
@@ -231,7 +248,10 @@ struct PlanBuilder {
     op.kind = kind;
     op.tpos[0] = (uint8_t)local_of[t];
     controls(op, ctrl);
-    if (U) op.coef = add_coefs(U, 4);
+    if (U) {
+      op.coef = add_coefs(U, 4);
+      for (int r = 0; r < 2; ++r) op.tj[r] = row_exp_biased(U, r, 2);
+    }
     out->ops.push_back(op);
     return true;
   }
@@ -244,6 +264,7 @@ struct PlanBuilder {
     op.tpos[1] = (uint8_t)local_of[t1];
     controls(op, ctrl);
     op.coef = add_coefs(U, 16);
+    for (int r = 0; r < 4; ++r) op.tj[r] = row_exp_biased(U, r, 4);
     out->ops.push_back(op);
     return true;
   }

@@ -11,7 +11,9 @@
 // consecutive threads on consecutive items so every access is coalesced once
 // the target is above the lowest qubits.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
+#include <type_traits>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -76,7 +78,21 @@ struct Mat2 {
 template <class P>
 struct Mat4 {
   typename P::Coef m[16];
+  int row_exp[4];  // float-float path: sum_k (|re| + |im|) of row r < 2^row_exp[r]
 };
+
+// Smallest e with sum_k (|re u_rk| + |im u_rk|) (as floats) < 2^e.
+static int row_exponent(const double* U, int row, int dim) {
+  double sum = 0.0;
+  for (int c = 0; c < dim; ++c) {
+    const double* z = U + 2 * (row * dim + c);
+    sum += std::fabs((double)(float)z[0]) + std::fabs((double)(float)z[1]);
+  }
+  if (sum == 0.0) return -126;
+  int e = 0;
+  std::frexp(sum, &e);  // sum = f 2^e, 0.5 <= f < 1, so sum < 2^e
+  return e;
+}
 
 constexpr int kThreads = 256;
 
@@ -135,10 +151,22 @@ __global__ void __launch_bounds__(kThreads) k_dense2(typename P::Amp* __restrict
       const uint64_t item = base + u * stride;
       if (item < n_items) {
         Val v[4] = {P::load(a[u][0]), P::load(a[u][1]), P::load(a[u][2]), P::load(a[u][3])};
-        psi[i0[u]] = P::template mac_round<4>(&g.m[0], v);
-        psi[i0[u] | b0] = P::template mac_round<4>(&g.m[4], v);
-        psi[i0[u] | b1] = P::template mac_round<4>(&g.m[8], v);
-        psi[i0[u] | b0 | b1] = P::template mac_round<4>(&g.m[12], v);
+        // Dense 4x4 rows (16 products) use the anchored accumulation; 2x2
+        // rows keep TwoSum, which stays exact when heads cancel (structured
+        // states such as Grover's, where every pair computes the same values
+        // and rounding errors would add coherently).
+        if constexpr (std::is_same<P, MathDF>::value) {
+          const int mexp = P::template max_exp_field<4>(v);
+          psi[i0[u]] = P::template mac_anchor_round<4>(&g.m[0], v, g.row_exp[0], mexp);
+          psi[i0[u] | b0] = P::template mac_anchor_round<4>(&g.m[4], v, g.row_exp[1], mexp);
+          psi[i0[u] | b1] = P::template mac_anchor_round<4>(&g.m[8], v, g.row_exp[2], mexp);
+          psi[i0[u] | b0 | b1] = P::template mac_anchor_round<4>(&g.m[12], v, g.row_exp[3], mexp);
+        } else {
+          psi[i0[u]] = P::template mac_round<4>(&g.m[0], v);
+          psi[i0[u] | b0] = P::template mac_round<4>(&g.m[4], v);
+          psi[i0[u] | b1] = P::template mac_round<4>(&g.m[8], v);
+          psi[i0[u] | b0 | b1] = P::template mac_round<4>(&g.m[12], v);
+        }
       }
     }
   }
@@ -359,6 +387,7 @@ static qs_status dense2_impl(qs_state s, int t0, int t1, uint64_t ctrl_mask, con
   DevInsert ins = to_dev(make_insert(with_ctrls({t0, t1}, ctrl_mask), ctrl_mask));
   Mat4<P> g;
   for (int j = 0; j < 16; ++j) g.m[j] = P::make_coef(U[2 * j], U[2 * j + 1]);
+  for (int r = 0; r < 4; ++r) g.row_exp[r] = row_exponent(U, r, 4);
   auto kern = k_dense2<P, ILP>;
   unsigned grid = grid_for(kern, items, ILP, s->device);
   kern<<<grid, kThreads, 0, s->stream>>>((typename P::Amp*)s->psi, items, 1ull << t0, 1ull << t1, ins, g);

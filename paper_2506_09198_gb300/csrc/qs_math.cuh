@@ -183,6 +183,36 @@ struct MathF32 {
   }
 };
 
+
+// Anchored float-float dot product.  The heads are summed into S starting
+// from a power-of-two anchor A >= 2 * (bound on |sum of heads|), so every
+// addition S + p has |S| >= |p| and its rounding error is exactly
+// p - (S' - S) (Fast2Sum, Dekker 1971: 3 operations instead of TwoSum's 6);
+// S - A is exact at the end (Sterbenz: S lies within [A/2, 2A]).  The bound
+// is sum_k |a_k| * max_k |x_k|: the row sum comes from the host as a power
+// of two exponent, the input maximum from the amplitudes.
+// With p = fl(a.h xh), s = fl(S + p) and d = S - s (exact: Fast2Sum), the two
+// exact error terms (a.h xh - p) + (p - (s - S)) equal a.h xh + d, so one fma
+// yields their sum rounded once: 7 packed operations per term.
+struct DF2AnchorAcc {
+  float2 S, C;
+  __device__ __forceinline__ void add(const DF2Term& a, float2 xh, float2 xl) {
+    const float2 p = mul2(a.h, xh);
+    const float2 s = add2(S, p);
+    const float2 t = fma2(a.h, xh, sub2(S, s));  // product tail + addition error
+    C = add2(C, t);
+    C = fma2(a.h, xl, C);
+    C = fma2(a.l, xh, C);
+    S = s;
+  }
+};
+
+// 2^(e - 127) as a float for an exponent field e clamped to [1, 254].
+__device__ __forceinline__ float pow2_field(int e) {
+  e = e < 1 ? 1 : (e > 254 ? 254 : e);
+  return __uint_as_float((uint32_t)e << 23);
+}
+
 struct MathDF {
   using Amp = double2;
   struct Val {
@@ -223,6 +253,38 @@ struct MathDF {
       acc.add(m[k].b, v[k].hs, v[k].ls);
     }
     return acc;
+  }
+  // Exponent field of the largest |head| among K input amplitudes.
+  template <int K>
+  static __device__ __forceinline__ int max_exp_field(const Val* v) {
+    float mx = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) mx = fmaxf(mx, fmaxf(fabsf(v[k].h.x), fabsf(v[k].h.y)));
+    return (int)(__float_as_uint(mx) >> 23);
+  }
+  // sum_k m[k] v[k] with the anchored accumulation; row_exp: the row's
+  // sum_k (|re m_k| + |im m_k|) < 2^row_exp; mexp: max_exp_field of v.
+  template <int K>
+  static __device__ __forceinline__ Amp mac_anchor_round(const Coef* m, const Val* v, int row_exp, int mexp) {
+    const DF2Acc r = mac_anchor<K>(m, v, row_exp, mexp);
+    return make_double2(f2d_exact(r.S.x) + f2d_exact(r.C.x), f2d_exact(r.S.y) + f2d_exact(r.C.y));
+  }
+  // Anchored accumulation returning (exact head sum, lower-order sum).
+  template <int K>
+  static __device__ __forceinline__ DF2Acc mac_anchor(const Coef* m, const Val* v, int row_exp, int mexp) {
+    const float A = pow2_field(mexp + row_exp + 2);
+    DF2AnchorAcc acc;
+    acc.S = make_float2(A, A);
+    acc.C = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      acc.add(m[k].a, v[k].h, v[k].l);
+      acc.add(m[k].b, v[k].hs, v[k].ls);
+    }
+    DF2Acc r;
+    r.S = sub2(acc.S, make_float2(A, A));
+    r.C = acc.C;
+    return r;
   }
   template <int K>
   static __device__ __forceinline__ Amp mac_round(const Coef* m, const Val* v) {

@@ -111,6 +111,12 @@ struct TileF32 {
   static __device__ __forceinline__ M::Val val(Sm s) { return M::load(s); }
   template <int K>
   static __device__ __forceinline__ Sm mac(const M::Coef* c, const M::Val* v) { return M::mac_round<K>(c, v); }
+  template <int K>
+  static __device__ __forceinline__ int mexp(const M::Val*) { return 0; }
+  template <int K>
+  static __device__ __forceinline__ Sm mac_rows(const M::Coef* c, const M::Val* v, int, int) {
+    return M::mac_round<K>(c, v);
+  }
   static __device__ __forceinline__ Sm neg(Sm a) {
     return make_float2(__uint_as_float(__float_as_uint(a.x) ^ 0x80000000u),
                        __uint_as_float(__float_as_uint(a.y) ^ 0x80000000u));
@@ -136,6 +142,12 @@ struct TileF64 {
   static __device__ __forceinline__ M::Val val(Sm s) { return M::load(s); }
   template <int K>
   static __device__ __forceinline__ Sm mac(const M::Coef* c, const M::Val* v) { return M::mac_round<K>(c, v); }
+  template <int K>
+  static __device__ __forceinline__ int mexp(const M::Val*) { return 0; }
+  template <int K>
+  static __device__ __forceinline__ Sm mac_rows(const M::Coef* c, const M::Val* v, int, int) {
+    return M::mac_round<K>(c, v);
+  }
   static __device__ __forceinline__ Sm neg(Sm a) { return make_double2(dneg(a.x), dneg(a.y)); }
   static __device__ __forceinline__ Sm mul_minus_i(Sm a) { return make_double2(a.y, dneg(a.x)); }
   static __device__ __forceinline__ Sm mul_i(Sm a) { return make_double2(dneg(a.y), a.x); }
@@ -173,6 +185,17 @@ struct TileDF {
     // Renormalise (S, C) to head and tail with Fast2Sum (Dekker 1971); C is
     // the lower-order part, so the head absorbs it and the tail keeps the
     // remainder.
+    const float2 s = add2(a.S, a.C);
+    const float2 e = sub2(a.C, sub2(s, a.S));
+    return make_float4(s.x, s.y, e.x, e.y);
+  }
+  template <int K>
+  static __device__ __forceinline__ int mexp(const M::Val* v) { return M::max_exp_field<K>(v); }
+  // Anchored accumulation for dense rows (row_exp from the host, mexp from
+  // the inputs), renormalised like mac.
+  template <int K>
+  static __device__ __forceinline__ Sm mac_rows(const M::Coef* c, const M::Val* v, int row_exp, int mx) {
+    const DF2Acc a = M::mac_anchor<K>(c, v, row_exp, mx);
     const float2 s = add2(a.S, a.C);
     const float2 e = sub2(a.C, sub2(s, a.S));
     return make_float4(s.x, s.y, e.x, e.y);
@@ -277,10 +300,11 @@ struct RegTile {
   }
 
   template <int K, bool CTRL>
-  __device__ __forceinline__ void dense1(const Coef* cf, uint32_t lmask) {
+  __device__ __forceinline__ void dense1(const Coef* cf, uint32_t lmask, const uint8_t* rexp) {
     Coef c[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) c[j] = cf[j];
+    (void)rexp;  // 2x2 rows keep TwoSum accumulation (exact under cancellation)
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (r & (1 << K)) continue;
@@ -304,17 +328,18 @@ struct RegTile {
   }
 
   template <int K0, int K1>
-  __device__ __forceinline__ void dense2(const Coef* cf, uint32_t lmask) {
+  __device__ __forceinline__ void dense2(const Coef* cf, uint32_t lmask, const uint8_t* rexp) {
     constexpr int B0 = 1 << K0, B1 = 1 << K1;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (r & (B0 | B1)) continue;
       if (lmask && ((toff | roff(r)) & lmask) != lmask) continue;
       const Val x[4] = {TP::val(v[r]), TP::val(v[r | B0]), TP::val(v[r | B1]), TP::val(v[r | B0 | B1])};
-      v[r] = TP::template mac<4>(cf, x);
-      v[r | B0] = TP::template mac<4>(cf + 4, x);
-      v[r | B1] = TP::template mac<4>(cf + 8, x);
-      v[r | B0 | B1] = TP::template mac<4>(cf + 12, x);
+      const int mx = TP::template mexp<4>(x);
+      v[r] = TP::template mac_rows<4>(cf, x, (int)rexp[0] - 128, mx);
+      v[r | B0] = TP::template mac_rows<4>(cf + 4, x, (int)rexp[1] - 128, mx);
+      v[r | B1] = TP::template mac_rows<4>(cf + 8, x, (int)rexp[2] - 128, mx);
+      v[r | B0 | B1] = TP::template mac_rows<4>(cf + 12, x, (int)rexp[3] - 128, mx);
     }
   }
 
@@ -371,12 +396,13 @@ struct RegTile {
 };
 
 template <class RT, int K>
-__device__ __forceinline__ void dense2_k1(RT& rt, int k1, const typename RT::Coef* cf, uint32_t lmask) {
+__device__ __forceinline__ void dense2_k1(RT& rt, int k1, const typename RT::Coef* cf, uint32_t lmask,
+                                          const uint8_t* rexp) {
   switch (k1) {
-    case 0: if constexpr (K != 0) rt.template dense2<K, 0>(cf, lmask); break;
-    case 1: if constexpr (K != 1) rt.template dense2<K, 1>(cf, lmask); break;
-    case 2: if constexpr (K != 2 && RT::RB > 2) rt.template dense2<K, (RT::RB > 2 ? 2 : 0)>(cf, lmask); break;
-    default: if constexpr (K != 3 && RT::RB > 3) rt.template dense2<K, (RT::RB > 3 ? 3 : 0)>(cf, lmask); break;
+    case 0: if constexpr (K != 0) rt.template dense2<K, 0>(cf, lmask, rexp); break;
+    case 1: if constexpr (K != 1) rt.template dense2<K, 1>(cf, lmask, rexp); break;
+    case 2: if constexpr (K != 2 && RT::RB > 2) rt.template dense2<K, (RT::RB > 2 ? 2 : 0)>(cf, lmask, rexp); break;
+    default: if constexpr (K != 3 && RT::RB > 3) rt.template dense2<K, (RT::RB > 3 ? 3 : 0)>(cf, lmask, rexp); break;
   }
 }
 
@@ -414,17 +440,17 @@ __device__ __forceinline__ void consume_tile(unsigned char* smem, const TileOp* 
       case TOP_DENSE1:
         if (op.lmask == 0) {
           switch (op.tpos[0]) {
-            case 0: rt.template dense1<0, false>(cf, 0); break;
-            case 1: rt.template dense1<1, false>(cf, 0); break;
-            case 2: if constexpr (RT::RB > 2) rt.template dense1<(RT::RB > 2 ? 2 : 0), false>(cf, 0); break;
-            default: if constexpr (RT::RB > 3) rt.template dense1<(RT::RB > 3 ? 3 : 0), false>(cf, 0); break;
+            case 0: rt.template dense1<0, false>(cf, 0, op.tj); break;
+            case 1: rt.template dense1<1, false>(cf, 0, op.tj); break;
+            case 2: if constexpr (RT::RB > 2) rt.template dense1<(RT::RB > 2 ? 2 : 0), false>(cf, 0, op.tj); break;
+            default: if constexpr (RT::RB > 3) rt.template dense1<(RT::RB > 3 ? 3 : 0), false>(cf, 0, op.tj); break;
           }
         } else {
           switch (op.tpos[0]) {
-            case 0: rt.template dense1<0, true>(cf, op.lmask); break;
-            case 1: rt.template dense1<1, true>(cf, op.lmask); break;
-            case 2: if constexpr (RT::RB > 2) rt.template dense1<(RT::RB > 2 ? 2 : 0), true>(cf, op.lmask); break;
-            default: if constexpr (RT::RB > 3) rt.template dense1<(RT::RB > 3 ? 3 : 0), true>(cf, op.lmask); break;
+            case 0: rt.template dense1<0, true>(cf, op.lmask, op.tj); break;
+            case 1: rt.template dense1<1, true>(cf, op.lmask, op.tj); break;
+            case 2: if constexpr (RT::RB > 2) rt.template dense1<(RT::RB > 2 ? 2 : 0), true>(cf, op.lmask, op.tj); break;
+            default: if constexpr (RT::RB > 3) rt.template dense1<(RT::RB > 3 ? 3 : 0), true>(cf, op.lmask, op.tj); break;
           }
         }
         break;
@@ -441,10 +467,10 @@ __device__ __forceinline__ void consume_tile(unsigned char* smem, const TileOp* 
       }
       case TOP_DENSE2:
         switch (op.tpos[0]) {
-          case 0: dense2_k1<RT, 0>(rt, op.tpos[1], cf, op.lmask); break;
-          case 1: dense2_k1<RT, 1>(rt, op.tpos[1], cf, op.lmask); break;
-          case 2: if constexpr (RT::RB > 2) dense2_k1<RT, (RT::RB > 2 ? 2 : 0)>(rt, op.tpos[1], cf, op.lmask); break;
-          default: if constexpr (RT::RB > 3) dense2_k1<RT, (RT::RB > 3 ? 3 : 0)>(rt, op.tpos[1], cf, op.lmask); break;
+          case 0: dense2_k1<RT, 0>(rt, op.tpos[1], cf, op.lmask, op.tj); break;
+          case 1: dense2_k1<RT, 1>(rt, op.tpos[1], cf, op.lmask, op.tj); break;
+          case 2: if constexpr (RT::RB > 2) dense2_k1<RT, (RT::RB > 2 ? 2 : 0)>(rt, op.tpos[1], cf, op.lmask, op.tj); break;
+          default: if constexpr (RT::RB > 3) dense2_k1<RT, (RT::RB > 3 ? 3 : 0)>(rt, op.tpos[1], cf, op.lmask, op.tj); break;
         }
         break;
       case TOP_PHASE:
