@@ -103,6 +103,11 @@ qs_status qs_copy_in(qs_state s, const void* host);
 /* Copy the whole state to host memory (same layout).  Synchronous. */
 qs_status qs_copy_out(qs_state s, void* host);
 
+/* Like qs_copy_out, but asynchronous on the state's stream: the copy is
+ * complete when the stream reaches this point (qs_sync).  host should be
+ * pinned (page-locked) so that the copy overlaps other streams' work. */
+qs_status qs_copy_out_async(qs_state s, void* host);
+
 /* host_out[j] = amplitude idx[j] (count entries, state's dtype), for
  * sampled checks of large states.  Synchronous.  Indices must be < 2^n. */
 qs_status qs_gather(qs_state s, const uint64_t* idx, int64_t count, void* host_out);

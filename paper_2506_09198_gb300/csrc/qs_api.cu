@@ -293,6 +293,14 @@ qs_status qs_copy_out(qs_state s, void* host) {
   return device_error_check(s);
 }
 
+qs_status qs_copy_out_async(qs_state s, void* host) {
+  qs_status st = check_state(s);
+  if (st != QS_OK) return st;
+  if (!host) return fail(QS_ERR_ARG, "host is NULL");
+  QS_CUDA(cudaMemcpyAsync(host, s->psi, amp_bytes(s->dtype) << s->n, cudaMemcpyDeviceToHost, s->stream));
+  return QS_OK;
+}
+
 qs_status qs_gather(qs_state s, const uint64_t* idx, int64_t count, void* host_out) {
   qs_status st = check_state(s);
   if (st != QS_OK) return st;

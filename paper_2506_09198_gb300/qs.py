@@ -68,6 +68,7 @@ _SIGS = {
     "qs_init_basis": [_P, ctypes.c_uint64],
     "qs_copy_in": [_P, _P],
     "qs_copy_out": [_P, _P],
+    "qs_copy_out_async": [_P, _P],
     "qs_gather": [_P, _PU64, ctypes.c_int64, _P],
     "qs_apply_1q": [_P, _I, _PD],
     "qs_apply_2q": [_P, _I, _I, _PD],
@@ -172,6 +173,13 @@ def qs_copy_out(h, host: np.ndarray):
     if not host.flags.c_contiguous or not host.flags.writeable:
         raise ValueError("host buffer must be contiguous and writeable")
     _check(_lib.qs_copy_out(h, _P(host.ctypes.data)))
+    return host
+
+
+def qs_copy_out_async(h, host: np.ndarray):
+    if not host.flags.c_contiguous or not host.flags.writeable:
+        raise ValueError("host buffer must be contiguous and writeable")
+    _check(_lib.qs_copy_out_async(h, _P(host.ctypes.data)))
     return host
 
 

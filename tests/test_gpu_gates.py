@@ -194,6 +194,10 @@ def test_init_copy_gather(mode):
     assert np.array_equal(st.read(), psi)
     idx = np.array([0, 1, 4097, (1 << n) - 1, 77], dtype=np.uint64)
     assert np.array_equal(st.gather(idx), psi[idx.astype(np.int64)])
+    out = np.zeros_like(psi)
+    qs().qs_copy_out_async(st.h, out)
+    st.sync()
+    assert np.array_equal(out, psi)
     st.close()
 
 
