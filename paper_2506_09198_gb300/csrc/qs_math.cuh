@@ -98,31 +98,29 @@ struct MathF64 {
 // Packed FP32x2 arithmetic (sm_100+): one instruction computes two lanes, so
 // the real and imaginary channels of a complex dot product share each issue.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long f2_bits(float2 a) {
-  return ((unsigned long long)__float_as_uint(a.y) << 32) | __float_as_uint(a.x);
-}
-__device__ __forceinline__ float2 bits_f2(unsigned long long r) {
-  return make_float2(__uint_as_float((uint32_t)r), __uint_as_float((uint32_t)(r >> 32)));
-}
-__device__ __forceinline__ float2 add2(float2 a, float2 b) {
-  unsigned long long d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
-  return bits_f2(d);
-}
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-  unsigned long long d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
-  return bits_f2(d);
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
-  unsigned long long d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
-  return bits_f2(d);
-}
+// Operands are packed into register pairs with mov.b64 {lo, hi}, which the
+// assembler resolves to the pair itself (no data movement).
+#define QS_F32X2_BINARY(name, op)                                                             \
+  __device__ __forceinline__ float2 name(float2 a, float2 b) {                               \
+    float2 d;                                                                                 \
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"     \
+        " " op " rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"                                     \
+        : "=f"(d.x), "=f"(d.y)                                                                \
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                            \
+    return d;                                                                                 \
+  }
+QS_F32X2_BINARY(add2, "add.rn.f32x2")
+QS_F32X2_BINARY(sub2, "sub.rn.f32x2")
+QS_F32X2_BINARY(mul2, "mul.rn.f32x2")
+#undef QS_F32X2_BINARY
+
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
-  return bits_f2(d);
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
 }
 
 // Float-float complex dot product on (re, im) channel pairs.

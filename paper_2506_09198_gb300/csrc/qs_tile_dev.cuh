@@ -229,6 +229,8 @@ struct RegTile {
   Sm v[R];
   uint32_t pbit[RB];  // local index bit of register bit j (0 when unused)
   uint32_t toff;      // local index bits of this thread
+  uint32_t tsw;       // swizzled byte offset of toff
+  uint32_t psw[RB];   // swizzled byte offset of pbit[j]
   int reff;           // registers in use (SMALL: tiles smaller than 2^RB)
   bool active;        // this thread holds amplitudes
 
@@ -270,8 +272,21 @@ struct RegTile {
       ++jt;
     }
     toff = t;
+    tsw = swz(t) * (uint32_t)sizeof(Sm);
+#pragma unroll
+    for (int j = 0; j < RB; ++j) psw[j] = swz(pbit[j]) * (uint32_t)sizeof(Sm);
     reff = 1 << rb;
     active = (tid >> (tile_log - rb)) == 0;
+  }
+
+  // Byte offsets: swz is linear over XOR on disjoint bits, so the swizzled
+  // offset of register r is the thread's offset XOR those of r's bits.
+  __device__ __forceinline__ uint32_t sw_off(int r) const {
+    uint32_t o = tsw;
+#pragma unroll
+    for (int j = 0; j < RB; ++j)
+      if ((r >> j) & 1) o ^= psw[j];
+    return o;
   }
 
   __device__ __forceinline__ void read_glob(const unsigned char* smem) {
@@ -281,16 +296,14 @@ struct RegTile {
       if (live(r) && active) v[r] = TP::to_sm(g[toff | roff(r)]);
   }
   __device__ __forceinline__ void read_sm(const unsigned char* smem) {
-    const Sm* t = reinterpret_cast<const Sm*>(smem);
 #pragma unroll
     for (int r = 0; r < R; ++r)
-      if (live(r) && active) v[r] = t[swz(toff | roff(r))];
+      if (live(r) && active) v[r] = *reinterpret_cast<const Sm*>(smem + sw_off(r));
   }
   __device__ __forceinline__ void write_sm(unsigned char* smem) const {
-    Sm* t = reinterpret_cast<Sm*>(smem);
 #pragma unroll
     for (int r = 0; r < R; ++r)
-      if (live(r) && active) t[swz(toff | roff(r))] = v[r];
+      if (live(r) && active) *reinterpret_cast<Sm*>(smem + sw_off(r)) = v[r];
   }
   __device__ __forceinline__ void write_glob(unsigned char* smem) const {
     Glob* g = reinterpret_cast<Glob*>(smem);
