@@ -190,7 +190,8 @@ qs_status qs_create(int n, qs_dtype dtype, qs_state* out) {
     return cuda_fail(e, "cudaMalloc(state)");
   }
   s->owns = true;
-  st = launch_init_basis(s, 0);
+  st = ensure_phase_tables(s->device);
+  if (st == QS_OK) st = launch_init_basis(s, 0);
   if (st == QS_OK) {
     e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) st = cuda_fail(e, "init");
@@ -223,6 +224,11 @@ qs_status qs_wrap(int n, qs_dtype dtype, void* device_ptr, void* stream, qs_stat
   s->psi = device_ptr;
   s->owns = false;
   s->stream = (cudaStream_t)stream;
+  st = ensure_phase_tables(s->device);
+  if (st != QS_OK) {
+    delete s;
+    return st;
+  }
   *out = s;
   return QS_OK;
 }

@@ -59,6 +59,7 @@ struct BatchArgs {
   const TileOp* ops;
   const typename TP::M::Coef* coefs;
   const uint8_t* perm;
+  const typename TP::Phase* phase_tab;
   uint32_t n_states;
   uint32_t* counter;  // next state to claim (zeroed before the launch)
   uint32_t* err;
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_batch(const Batc
     Sm* t = reinterpret_cast<Sm*>(smem + (size_t)s * kMaxTileBytes);
     const uint64_t base = tile_base(d.tau, b.L, b.m, b.base_high);
     consume_tile<TP>(reinterpret_cast<unsigned char*>(t), a.ops + b.op0, b.nops, a.coefs + b.coef0,
-                     a.perm + b.perm0, b.L + b.m, base, tid);
+                     a.perm + b.perm0, a.phase_tab, b.L + b.m, base, tid);
     fence_async_smem();
     mbar_arrive(&done[s]);
   }
@@ -265,6 +266,7 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
       if (emitted == 0) return fail(QS_ERR_UNSUPPORTED, "batch state %d: gate %zu could not be placed", i, next);
       if (bo.ops.empty()) continue;
       bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits, TP::kBankBits);
+      group_terms(bo.ops);
       BatchBlock b;
       std::memset(&b, 0, sizeof(b));
       b.L = geom.L;
@@ -345,6 +347,8 @@ qs_status launch_batch(qs_state s0, BatchCache* bc, cudaStream_t stream) {
   args.ops = (const TileOp*)(base + bc->off_ops);
   args.coefs = (const typename TP::M::Coef*)(base + bc->off_coefs);
   args.perm = base + bc->off_perm;
+  args.phase_tab = static_cast<const typename TP::Phase*>(phase_table(s0->device, TP::kPhaseFormat));
+  if (!args.phase_tab) return fail(QS_ERR_CUDA, "phase tables missing on device %d", s0->device);
   args.n_states = bc->n_states;
   args.counter = (uint32_t*)(base + bc->off_counter);
   args.err = device_error_word(s0->device);

@@ -22,6 +22,20 @@ namespace fuser {
 
 inline bool is_c(const double* z, double re, double im) { return z[0] == re && z[1] == im; }
 
+// A coefficient on the 2^-32-turn grid: c = exp(2 pi i m / 2^32) to within
+// 1e-15 per component (the rounding of cos and sin).
+inline bool dyadic_turn(const double* c, uint32_t* m) {
+  const double t = std::atan2(c[1], c[0]) * (4294967296.0 / 6.283185307179586476925286766559);
+  const double r = std::nearbyint(t);
+  if (!(std::fabs(t - r) <= 1e-3)) return false;
+  const uint32_t mm = (uint32_t)(uint64_t)(int64_t)r;
+  double cr, ci;
+  turn_cos_sin(mm, &cr, &ci);
+  if (!(std::fabs(cr - c[0]) <= 1e-15 && std::fabs(ci - c[1]) <= 1e-15)) return false;
+  *m = mm;
+  return true;
+}
+
 // Smallest e with sum_c (|re u_rc| + |im u_rc|) (entries rounded to float)
 // < 2^e, stored biased by 128: the anchored float-float accumulation of
 // dense rows needs this bound.
@@ -193,8 +207,17 @@ struct PlanBuilder {
         if (one) op.gpat |= 1ull << q;
       }
     }
+    // Phases on the 2^-32-turn grid become terms; group_terms turns runs
+    // of them into TOP_POLY runs and the rest back into PHASE / NEG ops.
+    uint32_t m = 0;
     if (is_c(c, -1, 0)) {
-      op.kind = TOP_NEG;
+      op.kind = TOP_TERM;
+      op.neg = 1;
+      op.ptab = 0x80000000u;
+    } else if (dyadic_turn(c, &m)) {
+      op.kind = TOP_TERM;
+      op.ptab = m;
+      op.coef = add_coefs(c, 1);
     } else {
       op.kind = TOP_PHASE;
       op.coef = add_coefs(c, 1);
@@ -270,6 +293,15 @@ struct PlanBuilder {
   }
 
   bool perm(const int* targets, int k, uint64_t ctrl, const uint32_t* p) {
+    if (k == 2 && ctrl == 0 && p[0] == 0 && p[1] == 2 && p[2] == 1 && p[3] == 3) {  // SWAP: relabel only
+      if (!room(1, 0, 0)) return false;
+      TileOp op = blank();
+      op.kind = TOP_SWAPBITS;
+      op.tpos[0] = (uint8_t)local_of[targets[0]];
+      op.tpos[1] = (uint8_t)local_of[targets[1]];
+      out->ops.push_back(op);
+      return true;
+    }
     if (k > 8 || !room(1, 0, 1 << k)) return false;
     TileOp op = blank();
     op.kind = TOP_PERM;
@@ -391,6 +423,7 @@ inline std::vector<TileOp> schedule_layouts(const std::vector<TileOp>& ops, int 
   auto make_layout = [&](size_t i) {
     uint32_t set = 0;
     for (size_t j = i; j < ops.size(); ++j) {
+      if (ops[j].kind == TOP_SWAPBITS) break;  // later needs refer to relabelled bits
       const uint32_t need = reg_need(ops[j]);
       if (!need) continue;
       const uint32_t u = set | need;
@@ -404,6 +437,20 @@ inline std::vector<TileOp> schedule_layouts(const std::vector<TileOp>& ops, int 
   for (size_t i = 0; i < ops.size(); ++i) {
     const uint32_t need = reg_need(ops[i]);
     if (!have || (need & ~cur)) make_layout(i);
+    if (ops[i].kind == TOP_SWAPBITS) {
+      // The register that held local bit a now holds bit b, and vice versa.
+      const int a = ops[i].tpos[0], b = ops[i].tpos[1];
+      const bool ra = (cur >> a) & 1u, rb_ = (cur >> b) & 1u;
+      if (ra && rb_) {
+        std::swap(pos_of[a], pos_of[b]);
+      } else if (ra || rb_) {
+        const int from = ra ? a : b, to = ra ? b : a;
+        cur = (cur & ~(1u << from)) | (1u << to);
+        pos_of[to] = pos_of[from];
+      }
+      out.push_back(ops[i]);
+      continue;
+    }
     TileOp op = ops[i];
     if (need) {
       op.tpos[0] = (uint8_t)pos_of[ops[i].tpos[0]];
@@ -415,6 +462,53 @@ inline std::vector<TileOp> schedule_layouts(const std::vector<TileOp>& ops, int 
   if (cur & low) emit(fill_high(0));  // bank-friendly last write
   return out;
 }
+
+// Runs of at least kPolyMinRun consecutive terms become TOP_POLY runs of at
+// most kPolyMaxRun terms; shorter runs go back to single PHASE / NEG ops.
+inline void group_terms(std::vector<TileOp>& ops) {
+  size_t i = 0;
+  while (i < ops.size()) {
+    if (ops[i].kind != TOP_TERM) {
+      ++i;
+      continue;
+    }
+    size_t j = i;
+    while (j < ops.size() && ops[j].kind == TOP_TERM) ++j;
+    if (j - i < (size_t)kPolyMinRun) {
+      for (size_t t = i; t < j; ++t) ops[t].kind = ops[t].neg ? TOP_NEG : TOP_PHASE;
+    } else {
+      for (size_t s = i; s < j; s += kPolyMaxRun) {
+        const size_t e = std::min(j, s + (size_t)kPolyMaxRun);
+        uint32_t any = 0;
+        for (size_t t = s; t < e; ++t) any |= ops[t].ptab;
+        TileOp& h = ops[s];
+        h.kind = TOP_POLY;
+        h.k = (uint8_t)(e - s);
+        // The sum of the m's has no bits below the lowest bit set in any m.
+        h.nloc = any == 0 ? 5 : any == 0x80000000u ? 4 : (uint8_t)(__builtin_ctz(any) / 8);
+      }
+    }
+    i = j;
+  }
+}
+
+// Ops that only move amplitudes or flip signs: a block of these runs exactly
+// in any precision policy.
+inline bool moves_only(const std::vector<TileOp>& ops) {
+  for (const TileOp& op : ops) {
+    switch (op.kind) {
+      case TOP_LAYOUT: case TOP_XSWAP: case TOP_Y: case TOP_NEG: case TOP_PERM: case TOP_SWAPBITS: break;
+      case TOP_POLY: if (op.nloc < 4) return false; break;
+      case TOP_TERM: break;
+      default: return false;
+    }
+  }
+  return true;
+}
+
+// Scheduled-op cost of one gate: an op, plus a layout change for gates that
+// need register bits (diagonal gates never do).
+inline int op_weight(const FGate& g) { return g.diagonal ? 1 : 2; }
 
 // Estimated pool use of one gate.
 inline void pool_need(const FGate& g, int* coefs, int* perm_bytes) {
@@ -433,10 +527,12 @@ inline void pool_need(const FGate& g, int* coefs, int* perm_bytes) {
 
 // Choose the next block starting at the first untaken gate.  Returns the
 // member indices (in application order) and the geometry; an empty result
-// means gate `next` cannot be placed in a tile with these limits.
+// means gate `next` cannot be placed in a tile with these limits.  With
+// perms_only, only permutation gates join (moves cost no arithmetic, so such
+// a block can take more high qubits than the arithmetic blocks).
 inline std::vector<size_t> choose_block(const std::vector<FGate>& gates, const std::vector<char>& taken, size_t next,
                                         int n, int tile_log, int max_high, int min_chunk_log, Limits lim,
-                                        size_t window, Geom* geom_out) {
+                                        size_t window, Geom* geom_out, bool perms_only = false) {
   std::vector<size_t> members;
   const FGate& g0 = gates[next];
   Geom geom;
@@ -447,17 +543,18 @@ inline std::vector<size_t> choose_block(const std::vector<FGate>& gates, const s
   for (size_t i = next; i < gates.size() && i < next + window; ++i) {
     if (taken[i]) continue;
     const FGate& g = gates[i];
-    bool ok = tileable(g) && !(g.qubit_mask & blocked);
+    bool ok = tileable(g) && !(g.qubit_mask & blocked) && (!perms_only || g.kind == QS_GATE_PERM);
     Geom trial;
     int c_need = 0, p_need = 0;
     pool_need(g, &c_need, &p_need);
     if (ok) ok = geometry(need | g.tmask, n, tile_log, max_high, min_chunk_log, &trial);
-    if (ok && (ops + 1 > lim.ops || coefs + c_need > lim.coefs || pbytes + p_need > lim.perm_bytes)) ok = false;
+    if (ok && (ops + op_weight(g) > lim.ops || coefs + c_need > lim.coefs || pbytes + p_need > lim.perm_bytes))
+      ok = false;
     if (ok) {
       members.push_back(i);
       need |= g.tmask;
       geom = trial;
-      ++ops;
+      ops += op_weight(g);
       coefs += c_need;
       pbytes += p_need;
     } else {

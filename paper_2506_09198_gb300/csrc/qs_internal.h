@@ -85,6 +85,15 @@ qs_status dispatch_uk(qs_state s, const int* targets, int k, uint64_t ctrl_mask,
 qs_status dispatch_diag(qs_state s, const int* targets, int k, uint64_t ctrl_mask, const double* d);
 qs_status dispatch_perm(qs_state s, const int* targets, int k, uint64_t ctrl_mask, const uint32_t* perm);
 
+// Phase tables for runs of phase terms (qs_phase.cu): entry 256 b + v is
+// exp(2 pi i (v 2^(8b)) / 2^32).  ensure_phase_tables fills them on the
+// current device (once; synchronous copies, so not inside a stream
+// capture); phase_table returns the device address of one format:
+// 0 float2, 1 double2, 2 float4 (re head, im head, re tail, im tail).
+void turn_cos_sin(uint32_t m, double* c, double* s);
+qs_status ensure_phase_tables(int device);
+const void* phase_table(int device, int format);
+
 qs_status ensure_scratch(qs_state s, size_t bytes);
 qs_status ensure_host_scratch(qs_state s, size_t bytes);
 

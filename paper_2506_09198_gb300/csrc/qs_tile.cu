@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_tile(typename TP
     Sm* t = reinterpret_cast<Sm*>(smem + (size_t)s * tile_bytes);
     const uint64_t base = tile_base(tau, plan.L, plan.m, plan.base_high);
     consume_tile<TP>(reinterpret_cast<unsigned char*>(t), plan.ops, plan.nops, plan.coefs, plan.perm,
-                     plan.L + plan.m, base, tid);
+                     static_cast<const typename TP::Phase*>(plan.phase_tab), plan.L + plan.m, base, tid);
     fence_async_smem();
     mbar_arrive(&done[s]);
   }
@@ -140,6 +141,10 @@ namespace {
 
 using namespace fuser;
 
+#ifndef QS_PERM_MAX_HIGH
+#define QS_PERM_MAX_HIGH 6
+#endif
+constexpr int kPermMaxHigh = QS_PERM_MAX_HIGH;  // high qubits of a permutation-only block
 constexpr int kMinChunkLog128 = 3;  // chunks of at least 128 bytes
 constexpr int kMinChunkLog64 = 4;
 
@@ -213,14 +218,41 @@ qs_status dispatch_single(qs_state s, const FGate& g) {
   return dispatch_uk(s, g.targets, g.k, g.ctrl, g.data);
 }
 
+// Translate, schedule and launch one block under policy TP.
+template <class TP>
+qs_status launch_block(qs_state s, const std::vector<FGate>& gates, const std::vector<size_t>& members,
+                       size_t count, const Geom& geom, Limits lim) {
+  using Coef = typename TP::M::Coef;
+  static thread_local BlockOut<Coef> bo;
+  static thread_local std::vector<unsigned char> plan_mem;
+  PlanBuilder<typename TP::M> pb(&bo, geom, lim);
+  for (size_t i = 0; i < count; ++i)
+    if (!pb.add(gates[members[i]])) return fail(QS_ERR_UNSUPPORTED, "block rebuild failed");
+  if (bo.ops.empty()) return QS_OK;
+  bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits, TP::kBankBits);
+  group_terms(bo.ops);
+  if (bo.ops.size() > (size_t)kTileMaxOps)
+    return fail(QS_ERR_UNSUPPORTED, "fused block of %zu ops exceeds %d", bo.ops.size(), kTileMaxOps);
+  const void* ptab = phase_table(s->device, TP::kPhaseFormat);
+  if (!ptab) return fail(QS_ERR_CUDA, "phase tables missing on device %d", s->device);
+  plan_mem.resize(sizeof(TilePlan<Coef>));
+  TilePlan<Coef>* plan = reinterpret_cast<TilePlan<Coef>*>(plan_mem.data());
+  fill_plan(plan, s->n, bo);
+  plan->phase_tab = ptab;
+  return launch_plan<TP>(s, *plan);
+}
+
 template <class TP>
 qs_status run_blocks(qs_state s, const std::vector<FGate>& gates, int max_high) {
   using Coef = typename TP::M::Coef;
   const int n = s->n;
   const int min_chunk = sizeof(typename TP::Glob) == 16 ? kMinChunkLog128 : kMinChunkLog64;
-  // Scheduling adds at most one layout change per gate, plus one before the
-  // first and one after the last.
-  const Limits lim{kTileMaxOps / 2 - 1, kTileMaxCoefs, kTileMaxPermBytes};
+  // Scheduling adds at most one layout change per non-diagonal gate (weight
+  // 2 in the op budget; diagonal gates weigh 1), plus one bank-friendly
+  // layout before the first op and one after the last.
+  const Limits lim{kTileMaxOps - 2, kTileMaxCoefs, kTileMaxPermBytes};
+  const void* ptab = phase_table(s->device, TP::kPhaseFormat);
+  if (!ptab) return fail(QS_ERR_CUDA, "phase tables missing on device %d", s->device);
   static thread_local std::vector<unsigned char> plan_mem;
   plan_mem.resize(sizeof(TilePlan<Coef>));
   TilePlan<Coef>* plan = reinterpret_cast<TilePlan<Coef>*>(plan_mem.data());
@@ -233,8 +265,15 @@ qs_status run_blocks(qs_state s, const std::vector<FGate>& gates, int max_high) 
       continue;
     }
     Geom geom;
-    const std::vector<size_t> members =
-        choose_block(gates, taken, next, n, TP::kTileLog, max_high, min_chunk, lim, 512, &geom);
+    std::vector<size_t> members;
+    if (gates[next].kind == QS_GATE_PERM && max_high < kPermMaxHigh) {
+      // Runs of permutations (the swap networks of QFTs) move amplitudes
+      // only: give them more high qubits than arithmetic blocks take.
+      members = choose_block(gates, taken, next, n, TP::kTileLog, kPermMaxHigh, min_chunk, lim, 512, &geom, true);
+      if (members.size() <= 1) members.clear();
+    }
+    if (members.empty())
+      members = choose_block(gates, taken, next, n, TP::kTileLog, max_high, min_chunk, lim, 512, &geom);
     // A gate that fits no tile, or a block of one gate (staging gains
     // nothing), runs on the per-gate kernels.
     if (members.size() <= 1) {
@@ -258,8 +297,21 @@ qs_status run_blocks(qs_state s, const std::vector<FGate>& gates, int max_high) 
     }
     if (!bo.ops.empty()) {
       bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits, TP::kBankBits);
-      fill_plan(plan, n, bo);
-      qs_status st = launch_plan<TP>(s, *plan);
+      group_terms(bo.ops);
+      if (bo.ops.size() > (size_t)kTileMaxOps)
+        return fail(QS_ERR_UNSUPPORTED, "fused block of %zu ops exceeds %d", bo.ops.size(), kTileMaxOps);
+      qs_status st;
+      if (std::is_same<TP, TileDF>::value && moves_only(bo.ops)) {
+        // Moves and sign flips are exact in any policy: the FP64 tile skips
+        // the float-float conversions (same tile size and layouts).
+        static_assert(TileF64::kTileLog == TileDF::kTileLog && TileF64::kRegBits == TileDF::kRegBits,
+                      "move-only blocks reuse the float-float geometry");
+        st = launch_block<TileF64>(s, gates, members, emitted, geom, lim);
+      } else {
+        fill_plan(plan, n, bo);
+        plan->phase_tab = ptab;
+        st = launch_plan<TP>(s, *plan);
+      }
       if (st != QS_OK) return st;
     }
   }

@@ -37,7 +37,19 @@ enum TileOpKind : uint8_t {
   TOP_PHASE = 5,   // multiply amplitudes with (lambda & lmask) == lpat by one coefficient
   TOP_NEG = 6,     // same with coefficient -1 (sign flip)
   TOP_DIAG = 7,    // d[s]: s from local targets tpos[0..nloc) (sub-register bits tj) and tile bits gq
-  TOP_PERM = 8     // permutation of local targets tpos[0..k), through shared memory
+  TOP_PERM = 8,    // permutation of local targets tpos[0..k), through shared memory
+  // A run of k phase terms (this op and the k - 1 TOP_TERM ops after it).
+  // Term t adds m_t = ptab (a phase in units of 2^-32 turn) to an amplitude's
+  // accumulator when (lambda & lmask) == lpat and (base & gmask) == gpat;
+  // the amplitude is then multiplied once by exp(2 pi i acc / 2^32), the
+  // product of four table entries (one per byte of acc, from byte nloc up).
+  // nloc 4: every m is 2^31, so the product is a sign; nloc 5: nothing to do.
+  TOP_POLY = 9,
+  TOP_TERM = 10,
+  // Swap of local bits tpos[0], tpos[1] (an uncontrolled SWAP gate): the
+  // amplitude a thread holds for local index lambda now belongs at the
+  // swapped index, so only the thread's index bookkeeping changes.
+  TOP_SWAPBITS = 11
 };
 
 // Before scheduling (host), dense gates carry local bit positions in tpos;
@@ -46,7 +58,7 @@ struct TileOp {
   uint8_t kind;
   uint8_t k;        // DIAG / PERM: number of targets; LAYOUT: register bits
   uint8_t nloc;     // DIAG: local targets
-  uint8_t pad0;
+  uint8_t neg;      // TERM before grouping: the term came from a sign flip
   uint8_t tpos[8];
   uint8_t tj[8];    // DIAG: sub-register bit of each local target
   uint8_t gq[8];    // DIAG: global qubit of target j when not local, else 0xFF
@@ -54,7 +66,7 @@ struct TileOp {
   uint32_t lpat;    // PHASE/NEG: local pattern
   uint64_t gmask, gpat;  // the op acts on a tile iff (base & gmask) == gpat
   uint32_t coef;    // first coefficient in the pool
-  uint32_t ptab;    // PERM: byte offset of the inverse table
+  uint32_t ptab;    // PERM: byte offset of the inverse table; POLY/TERM: m
 };
 
 template <class Coef>
@@ -68,6 +80,12 @@ struct TilePlan {
   TileOp ops[kTileMaxOps];
   Coef coefs[kTileMaxCoefs];
   uint8_t perm[kTileMaxPermBytes];
+  const void* phase_tab;               // exp(2 pi i v 2^(8b) / 2^32) at [256 b + v], the policy's format
 };
+
+// Phase terms: runs shorter than this stay single phase ops; a run holds at
+// most 255 terms (its count is a byte).
+constexpr int kPolyMinRun = 4;
+constexpr int kPolyMaxRun = 255;
 
 }  // namespace qs

@@ -124,6 +124,15 @@ struct TileF32 {
   // -i (x + iy) = y - ix
   static __device__ __forceinline__ Sm mul_minus_i(Sm a) { return make_float2(a.y, -a.x); }
   static __device__ __forceinline__ Sm mul_i(Sm a) { return make_float2(-a.y, a.x); }
+  // Phase-table entries (cos, sin) and sign flips under bit 31 of s.
+  using Phase = float2;
+  static constexpr int kPhaseFormat = 0;
+  static __device__ __forceinline__ M::Coef phase_coef(Phase p) {
+    return M::Coef{make_float2(p.x, p.x), make_float2(-p.y, p.y)};
+  }
+  static __device__ __forceinline__ Sm neg_if(Sm a, uint32_t s) {
+    return make_float2(__uint_as_float(__float_as_uint(a.x) ^ s), __uint_as_float(__float_as_uint(a.y) ^ s));
+  }
 };
 
 __device__ __forceinline__ double dneg(double x) {
@@ -151,6 +160,13 @@ struct TileF64 {
   static __device__ __forceinline__ Sm neg(Sm a) { return make_double2(dneg(a.x), dneg(a.y)); }
   static __device__ __forceinline__ Sm mul_minus_i(Sm a) { return make_double2(a.y, dneg(a.x)); }
   static __device__ __forceinline__ Sm mul_i(Sm a) { return make_double2(dneg(a.y), a.x); }
+  using Phase = double2;
+  static constexpr int kPhaseFormat = 1;
+  static __device__ __forceinline__ M::Coef phase_coef(Phase p) { return M::Coef{p.x, p.y}; }
+  static __device__ __forceinline__ double dneg_if(double x, uint32_t s) {
+    return __hiloint2double(__double2hiint(x) ^ (int)s, __double2loint(x));
+  }
+  static __device__ __forceinline__ Sm neg_if(Sm a, uint32_t s) { return make_double2(dneg_if(a.x, s), dneg_if(a.y, s)); }
 };
 
 // Float-float tile element: (re_h, im_h, re_l, im_l), |l| <= ulp(h)/2.
@@ -204,6 +220,23 @@ struct TileDF {
   static __device__ __forceinline__ Sm neg(Sm a) { return make_float4(fneg(a.x), fneg(a.y), fneg(a.z), fneg(a.w)); }
   static __device__ __forceinline__ Sm mul_minus_i(Sm a) { return make_float4(a.y, fneg(a.x), a.w, fneg(a.z)); }
   static __device__ __forceinline__ Sm mul_i(Sm a) { return make_float4(fneg(a.y), a.x, fneg(a.w), a.z); }
+  // Phase-table entries: (cos head, sin head, cos tail, sin tail).
+  using Phase = float4;
+  static constexpr int kPhaseFormat = 2;
+  static __device__ __forceinline__ M::Coef phase_coef(Phase p) {
+    M::Coef c;
+    c.a.h = make_float2(p.x, p.x);
+    c.a.hn = make_float2(-p.x, -p.x);
+    c.a.l = make_float2(p.z, p.z);
+    c.b.h = make_float2(-p.y, p.y);
+    c.b.hn = make_float2(p.y, -p.y);
+    c.b.l = make_float2(-p.w, p.w);
+    return c;
+  }
+  static __device__ __forceinline__ float fxor(float x, uint32_t s) { return __uint_as_float(__float_as_uint(x) ^ s); }
+  static __device__ __forceinline__ Sm neg_if(Sm a, uint32_t s) {
+    return make_float4(fxor(a.x, s), fxor(a.y, s), fxor(a.z, s), fxor(a.w, s));
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -277,6 +310,21 @@ struct RegTile {
     for (int j = 0; j < RB; ++j) psw[j] = swz(pbit[j]) * (uint32_t)sizeof(Sm);
     reff = 1 << rb;
     active = (tid >> (tile_log - rb)) == 0;
+  }
+
+  // Relabel for a swap of local bits a and b (no data moves).
+  __device__ __forceinline__ void swap_bits(int a, int b) {
+    auto sw = [a, b](uint32_t x) {
+      const uint32_t d = ((x >> a) ^ (x >> b)) & 1u;
+      return x ^ ((d << a) | (d << b));
+    };
+    toff = sw(toff);
+    tsw = swz(toff) * (uint32_t)sizeof(Sm);
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      pbit[j] = sw(pbit[j]);
+      psw[j] = swz(pbit[j]) * (uint32_t)sizeof(Sm);
+    }
   }
 
   // Byte offsets: swz is linear over XOR on disjoint bits, so the swizzled
@@ -385,6 +433,61 @@ struct RegTile {
     }
   }
 
+  // A run of phase terms (t[0] is the TOP_POLY op): sum each amplitude's
+  // phase on the 2^-32-turn grid in an integer, then multiply once by the
+  // table entries of its bytes (or flip signs when only bit 31 can be set).
+  __device__ __forceinline__ void poly(const TileOp* __restrict__ t, uint64_t base,
+                                       const typename TP::Phase* __restrict__ tab) {
+    const int count = t[0].k;
+    const int first = t[0].nloc;
+    if (first > 4) return;
+    uint32_t regmask = 0;
+#pragma unroll
+    for (int j = 0; j < RB; ++j) regmask |= pbit[j];
+    uint32_t acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0u;
+    uint32_t acc_t = 0;  // terms on thread bits only: the same for all of a thread's registers
+    for (int i = 0; i < count; ++i) {
+      const TileOp& op = t[i];
+      if ((base & op.gmask) != op.gpat) continue;
+      const uint32_t lmask = op.lmask, m = op.ptab;
+      if ((lmask & regmask) == 0u) {  // uniform: every thread has the same layout
+        acc_t += (toff & lmask) == op.lpat ? m : 0u;
+        continue;
+      }
+      // (toff | roff(r)) & lmask == lpat  <=>  roff(r) & lmask == x  (disjoint bits)
+      const uint32_t x = (toff & lmask) ^ op.lpat;
+      uint32_t pm[RB];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) pm[j] = pbit[j] & lmask;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        uint32_t q = 0;
+#pragma unroll
+        for (int j = 0; j < RB; ++j)
+          if ((r >> j) & 1) q |= pm[j];
+        acc[r] += q == x ? m : 0u;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] += acc_t;
+    if (first == 4) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = TP::neg_if(v[r], acc[r] & 0x80000000u);
+      return;
+    }
+    for (int b = first; b < 4; ++b) {
+      const typename TP::Phase* tb = tab + 256 * b;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const Coef c = TP::phase_coef(__ldg(tb + ((acc[r] >> (8 * b)) & 255u)));
+        const Val xv = TP::val(v[r]);
+        v[r] = TP::template mac<1>(&c, &xv);
+      }
+    }
+  }
+
   // Permutation of local targets: through shared memory (write in place,
   // read each destination's source).
   __device__ __forceinline__ void perm(const TileOp& op, const uint8_t* inv, unsigned char* smem) {
@@ -425,14 +528,20 @@ __device__ __forceinline__ void dense2_k1(RT& rt, int k1, const typename RT::Coe
 template <class TP>
 __device__ __forceinline__ void consume_tile(unsigned char* smem, const TileOp* __restrict__ ops, int nops,
                                              const typename TP::M::Coef* __restrict__ coefs,
-                                             const uint8_t* __restrict__ perm_tables, int tile_log, uint64_t base,
-                                             int tid) {
+                                             const uint8_t* __restrict__ perm_tables,
+                                             const typename TP::Phase* __restrict__ phase_tab, int tile_log,
+                                             uint64_t base, int tid) {
   using RT = RegTile<TP>;
   RT rt;
   const int rb = tile_log < RT::RB ? tile_log : RT::RB;
   bool first = true;
   for (int o = 0; o < nops; ++o) {
     const TileOp& op = ops[o];
+    if (op.kind == TOP_POLY) {  // the run's own terms carry their tile predicates
+      if (rt.active) rt.poly(ops + o, base, phase_tab);
+      o += op.k > 0 ? op.k - 1 : 0;
+      continue;
+    }
     if ((base & op.gmask) != op.gpat) continue;
     if (!rt.active && op.kind != TOP_LAYOUT && op.kind != TOP_PERM) continue;
     const typename RT::Coef* cf = coefs + op.coef;
@@ -497,6 +606,9 @@ __device__ __forceinline__ void consume_tile(unsigned char* smem, const TileOp* 
         break;
       case TOP_PERM:
         rt.perm(op, perm_tables + op.ptab, smem);
+        break;
+      case TOP_SWAPBITS:
+        rt.swap_bits(op.tpos[0], op.tpos[1]);
         break;
     }
   }

@@ -152,3 +152,46 @@ def test_dense_three_qubit_gate_rejected():
         st.run([W.gk((0, 2, 4), W.haar_unitary(8, W.rng_for(1)))])
     assert e.value.status == q.QS_ERR_UNSUPPORTED
     st.close()
+
+
+def swap_heavy_circuit(n, n_gates, seed):
+    """SWAPs (relabelled inside a block, no data movement) interleaved with
+    dense, controlled and phase gates whose qubits the SWAPs exchange."""
+    rng = W.rng_for(seed)
+    gates = [W.H(q) for q in range(n)]
+    for _ in range(n_gates):
+        r = int(rng.integers(6))
+        if r <= 1:
+            gates.append(W.SWAP(*W.random_distinct(rng, n, 2)))
+        elif r == 2:
+            gates.append(W.g1(int(rng.integers(n)), W.haar_unitary(2, rng)))
+        elif r == 3:
+            q = W.random_distinct(rng, n, 3)
+            gates.append(W.gk(q[:2], W.haar_unitary(4, rng), ctrls=q[2:] if rng.integers(2) else []))
+        elif r == 4:
+            gates.append(W.CP(*W.random_distinct(rng, n, 2), float(rng.uniform(0, 6.3))))
+        else:
+            q = W.random_distinct(rng, n, 3)
+            gates.append(W.gperm(q[:2], [0, 2, 1, 3], ctrls=q[2:]))  # a controlled SWAP moves data
+    return gates
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n,max_fuse", [(7, 3), (12, 3), (15, 2), (15, 5)])
+def test_swap_relabel(mode, n, max_fuse):
+    gates = swap_heavy_circuit(n, 60, seed=8500 + n + max_fuse)
+    psi0 = W.random_state(n, W.rng_for(8501))
+    ref = O.run_circuit(psi0.copy(), gates)
+    got = run_gpu(n, mode, gates, psi0, max_fuse)
+    assert_close(got, ref, mode, f"swap relabel n={n}")
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_swap_network_moves_exactly(mode):
+    """A register reversal by SWAPs alone moves amplitudes bit for bit."""
+    n = 17
+    gates = [W.SWAP(q, n - 1 - q) for q in range(n // 2)]
+    psi0 = W.random_state(n, W.rng_for(8600))
+    ref = O.run_circuit(psi0.copy(), gates)
+    got = run_gpu(n, mode, gates, psi0, 3)
+    assert np.array_equal(got, ref.astype(got.dtype))
