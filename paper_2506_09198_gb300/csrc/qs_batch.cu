@@ -265,8 +265,8 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
       }
       if (emitted == 0) return fail(QS_ERR_UNSUPPORTED, "batch state %d: gate %zu could not be placed", i, next);
       if (bo.ops.empty()) continue;
-      bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits, TP::kBankBits);
       group_terms(bo.ops);
+      bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits, TP::kBankBits);
       BatchBlock b;
       std::memset(&b, 0, sizeof(b));
       b.L = geom.L;

@@ -451,6 +451,37 @@ inline std::vector<TileOp> schedule_layouts(const std::vector<TileOp>& ops, int 
       out.push_back(ops[i]);
       continue;
     }
+    if (ops[i].kind == TOP_POLY) {
+      // Split each term's local condition into its thread bits (lmask,
+      // lpat) and its register bits (tj[0], tj[1] in register-index space),
+      // then order the run's terms by register condition (they commute), so
+      // that the kernel sums each group per thread and adds it to the
+      // group's registers once.
+      const size_t cnt = ops[i].k;
+      std::vector<TileOp> run(ops.begin() + i, ops.begin() + i + cnt);
+      const uint8_t count = run[0].k, first = run[0].nloc;
+      for (TileOp& t : run) {
+        uint32_t rm = 0, rp = 0;
+        for (int b = 0; b < tile_log; ++b) {
+          if (!((cur >> b) & 1u) || !((t.lmask >> b) & 1u)) continue;
+          rm |= 1u << pos_of[b];
+          if ((t.lpat >> b) & 1u) rp |= 1u << pos_of[b];
+        }
+        t.tj[0] = (uint8_t)rm;
+        t.tj[1] = (uint8_t)rp;
+        t.lmask &= ~cur;
+        t.lpat &= ~cur;
+      }
+      std::stable_sort(run.begin(), run.end(), [](const TileOp& x, const TileOp& y) {
+        return x.tj[0] != y.tj[0] ? x.tj[0] < y.tj[0] : x.tj[1] < y.tj[1];
+      });
+      for (size_t t = 0; t < cnt; ++t) run[t].kind = t == 0 ? TOP_POLY : TOP_TERM;
+      run[0].k = count;
+      run[0].nloc = first;
+      out.insert(out.end(), run.begin(), run.end());
+      i += cnt - 1;
+      continue;
+    }
     TileOp op = ops[i];
     if (need) {
       op.tpos[0] = (uint8_t)pos_of[ops[i].tpos[0]];
@@ -465,6 +496,8 @@ inline std::vector<TileOp> schedule_layouts(const std::vector<TileOp>& ops, int 
 
 // Runs of at least kPolyMinRun consecutive terms become TOP_POLY runs of at
 // most kPolyMaxRun terms; shorter runs go back to single PHASE / NEG ops.
+// Runs before schedule_layouts, which then splits each term's condition
+// into thread and register bits.
 inline void group_terms(std::vector<TileOp>& ops) {
   size_t i = 0;
   while (i < ops.size()) {

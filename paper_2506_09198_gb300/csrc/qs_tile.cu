@@ -229,8 +229,8 @@ qs_status launch_block(qs_state s, const std::vector<FGate>& gates, const std::v
   for (size_t i = 0; i < count; ++i)
     if (!pb.add(gates[members[i]])) return fail(QS_ERR_UNSUPPORTED, "block rebuild failed");
   if (bo.ops.empty()) return QS_OK;
-  bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits, TP::kBankBits);
   group_terms(bo.ops);
+  bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits, TP::kBankBits);
   if (bo.ops.size() > (size_t)kTileMaxOps)
     return fail(QS_ERR_UNSUPPORTED, "fused block of %zu ops exceeds %d", bo.ops.size(), kTileMaxOps);
   const void* ptab = phase_table(s->device, TP::kPhaseFormat);
@@ -296,8 +296,8 @@ qs_status run_blocks(qs_state s, const std::vector<FGate>& gates, int max_high) 
       continue;
     }
     if (!bo.ops.empty()) {
-      bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits, TP::kBankBits);
       group_terms(bo.ops);
+      bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits, TP::kBankBits);
       if (bo.ops.size() > (size_t)kTileMaxOps)
         return fail(QS_ERR_UNSUPPORTED, "fused block of %zu ops exceeds %d", bo.ops.size(), kTileMaxOps);
       qs_status st;

@@ -39,11 +39,14 @@ enum TileOpKind : uint8_t {
   TOP_DIAG = 7,    // d[s]: s from local targets tpos[0..nloc) (sub-register bits tj) and tile bits gq
   TOP_PERM = 8,    // permutation of local targets tpos[0..k), through shared memory
   // A run of k phase terms (this op and the k - 1 TOP_TERM ops after it).
-  // Term t adds m_t = ptab (a phase in units of 2^-32 turn) to an amplitude's
-  // accumulator when (lambda & lmask) == lpat and (base & gmask) == gpat;
-  // the amplitude is then multiplied once by exp(2 pi i acc / 2^32), the
-  // product of four table entries (one per byte of acc, from byte nloc up).
-  // nloc 4: every m is 2^31, so the product is a sign; nloc 5: nothing to do.
+  // Term t adds m_t = ptab (a phase in units of 2^-32 turn) to the
+  // accumulator of the amplitude a thread holds in register r when the
+  // thread bits match, (lambda & lmask) == lpat, the register bits match,
+  // (r & tj[0]) == tj[1], and the tile matches, (base & gmask) == gpat.
+  // Terms come grouped by (tj[0], tj[1]).  The amplitude is then multiplied
+  // once by exp(2 pi i acc / 2^32), the product of four table entries (one
+  // per byte of acc, from byte nloc up); nloc 4: every m is 2^31, so the
+  // product is a sign; nloc 5: nothing to do.
   TOP_POLY = 9,
   TOP_TERM = 10,
   // Swap of local bits tpos[0], tpos[1] (an uncontrolled SWAP gate): the

@@ -436,42 +436,33 @@ struct RegTile {
   // A run of phase terms (t[0] is the TOP_POLY op): sum each amplitude's
   // phase on the 2^-32-turn grid in an integer, then multiply once by the
   // table entries of its bytes (or flip signs when only bit 31 can be set).
+  // Terms with the same register condition are summed per thread first.
+  __device__ __forceinline__ void add_group(uint32_t* acc, uint32_t rm, uint32_t rp, uint32_t g) const {
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] += ((uint32_t)r & rm) == rp ? g : 0u;
+  }
   __device__ __forceinline__ void poly(const TileOp* __restrict__ t, uint64_t base,
                                        const typename TP::Phase* __restrict__ tab) {
     const int count = t[0].k;
     const int first = t[0].nloc;
     if (first > 4) return;
-    uint32_t regmask = 0;
-#pragma unroll
-    for (int j = 0; j < RB; ++j) regmask |= pbit[j];
     uint32_t acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0u;
-    uint32_t acc_t = 0;  // terms on thread bits only: the same for all of a thread's registers
+    uint32_t g = 0, grm = t[0].tj[0], grp = t[0].tj[1];
     for (int i = 0; i < count; ++i) {
       const TileOp& op = t[i];
+      const uint32_t rm = op.tj[0], rp = op.tj[1];
+      if (rm != grm || rp != grp) {  // uniform: the same plan for every thread
+        add_group(acc, grm, grp, g);
+        g = 0;
+        grm = rm;
+        grp = rp;
+      }
       if ((base & op.gmask) != op.gpat) continue;
-      const uint32_t lmask = op.lmask, m = op.ptab;
-      if ((lmask & regmask) == 0u) {  // uniform: every thread has the same layout
-        acc_t += (toff & lmask) == op.lpat ? m : 0u;
-        continue;
-      }
-      // (toff | roff(r)) & lmask == lpat  <=>  roff(r) & lmask == x  (disjoint bits)
-      const uint32_t x = (toff & lmask) ^ op.lpat;
-      uint32_t pm[RB];
-#pragma unroll
-      for (int j = 0; j < RB; ++j) pm[j] = pbit[j] & lmask;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        uint32_t q = 0;
-#pragma unroll
-        for (int j = 0; j < RB; ++j)
-          if ((r >> j) & 1) q |= pm[j];
-        acc[r] += q == x ? m : 0u;
-      }
+      g += (toff & op.lmask) == op.lpat ? op.ptab : 0u;
     }
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] += acc_t;
+    add_group(acc, grm, grp, g);
     if (first == 4) {
 #pragma unroll
       for (int r = 0; r < R; ++r) v[r] = TP::neg_if(v[r], acc[r] & 0x80000000u);
