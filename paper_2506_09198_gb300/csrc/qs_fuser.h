@@ -273,7 +273,8 @@ struct PlanBuilder {
     controls(op, ctrl);
     if (U) {
       op.coef = add_coefs(U, 4);
-      for (int r = 0; r < 2; ++r) op.tj[r] = row_exp_biased(U, r, 2);
+      // Real matrices (H, rotations about y) skip the imaginary terms.
+      op.nloc = (U[1] == 0.0 && U[3] == 0.0 && U[5] == 0.0 && U[7] == 0.0) ? 1 : 0;
     }
     out->ops.push_back(op);
     return true;
@@ -478,6 +479,24 @@ inline std::vector<TileOp> schedule_layouts(const std::vector<TileOp>& ops, int 
       for (size_t t = 0; t < cnt; ++t) run[t].kind = t == 0 ? TOP_POLY : TOP_TERM;
       run[0].k = count;
       run[0].nloc = first;
+      // Complex multiplications per thread: accumulate mode, one per
+      // register and byte; factored mode, a table product per group plus
+      // one per matching register and group.
+      if (first < 4) {
+        const int R = 1 << rb, bytes = 4 - first;
+        int fact = 0;
+        for (size_t g0 = 0; g0 < cnt;) {
+          size_t g1 = g0 + 1;
+          while (g1 < cnt && run[g1].tj[0] == run[g0].tj[0] && run[g1].tj[1] == run[g0].tj[1]) ++g1;
+          uint32_t any = 0;
+          for (size_t t = g0; t < g1; ++t) any |= run[t].ptab;
+          const int gfirst = any == 0 ? 3 : __builtin_ctz(any) / 8;  // the group's lowest nonzero byte
+          for (size_t t = g0; t < g1; ++t) run[t].tj[2] = (uint8_t)gfirst;
+          fact += (4 - gfirst) + (R >> __builtin_popcount(run[g0].tj[0]));
+          g0 = g1;
+        }
+        run[0].tpos[0] = fact < bytes * R ? 1 : 0;
+      }
       out.insert(out.end(), run.begin(), run.end());
       i += cnt - 1;
       continue;

@@ -30,7 +30,7 @@ constexpr int kTileMaxPermBytes = 512;
 // (TOP_LAYOUT) so that every dense gate finds its targets in registers.
 enum TileOpKind : uint8_t {
   TOP_LAYOUT = 0,  // new layout: register bit j = local bit tpos[j]
-  TOP_DENSE1 = 1,  // 2x2 on register bit tpos[0]
+  TOP_DENSE1 = 1,  // 2x2 on register bit tpos[0]; nloc = 1: real coefficients
   TOP_DENSE2 = 2,  // 4x4 on register bits tpos[0], tpos[1] (index b0 + 2 b1)
   TOP_XSWAP = 3,   // swap pair partners on register bit tpos[0]
   TOP_Y = 4,       // up' = -i lo, lo' = i up on register bit tpos[0]
@@ -46,7 +46,10 @@ enum TileOpKind : uint8_t {
   // Terms come grouped by (tj[0], tj[1]).  The amplitude is then multiplied
   // once by exp(2 pi i acc / 2^32), the product of four table entries (one
   // per byte of acc, from byte nloc up); nloc 4: every m is 2^31, so the
-  // product is a sign; nloc 5: nothing to do.
+  // product is a sign; nloc 5: nothing to do.  tpos[0] = 1 (factored): each
+  // group's sum is turned into its phase once per thread and multiplied into
+  // the group's registers instead, starting at the group's lowest nonzero
+  // byte tj[2].
   TOP_POLY = 9,
   TOP_TERM = 10,
   // Swap of local bits tpos[0], tpos[1] (an uncontrolled SWAP gate): the

@@ -111,6 +111,14 @@ struct TileF32 {
   static __device__ __forceinline__ M::Val val(Sm s) { return M::load(s); }
   template <int K>
   static __device__ __forceinline__ Sm mac(const M::Coef* c, const M::Val* v) { return M::mac_round<K>(c, v); }
+  // Real coefficients: the (-mi, mi) terms are zero and skipped.
+  template <int K>
+  static __device__ __forceinline__ Sm mac_real(const M::Coef* c, const M::Val* v) {
+    float2 acc = mul2(c[0].a, v[0].v);
+#pragma unroll
+    for (int k = 1; k < K; ++k) acc = fma2(c[k].a, v[k].v, acc);
+    return acc;
+  }
   template <int K>
   static __device__ __forceinline__ int mexp(const M::Val*) { return 0; }
   template <int K>
@@ -151,6 +159,16 @@ struct TileF64 {
   static __device__ __forceinline__ M::Val val(Sm s) { return M::load(s); }
   template <int K>
   static __device__ __forceinline__ Sm mac(const M::Coef* c, const M::Val* v) { return M::mac_round<K>(c, v); }
+  template <int K>
+  static __device__ __forceinline__ Sm mac_real(const M::Coef* c, const M::Val* v) {
+    double re = 0.0, im = 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      re = __fma_rn(c[k].re, v[k].re, re);
+      im = __fma_rn(c[k].re, v[k].im, im);
+    }
+    return make_double2(re, im);
+  }
   template <int K>
   static __device__ __forceinline__ int mexp(const M::Val*) { return 0; }
   template <int K>
@@ -201,6 +219,16 @@ struct TileDF {
     // Renormalise (S, C) to head and tail with Fast2Sum (Dekker 1971); C is
     // the lower-order part, so the head absorbs it and the tail keeps the
     // remainder.
+    const float2 s = add2(a.S, a.C);
+    const float2 e = sub2(a.C, sub2(s, a.S));
+    return make_float4(s.x, s.y, e.x, e.y);
+  }
+  template <int K>
+  static __device__ __forceinline__ Sm mac_real(const M::Coef* c, const M::Val* v) {
+    DF2Acc a;
+    a.first(c[0].a, v[0].h, v[0].l);
+#pragma unroll
+    for (int k = 1; k < K; ++k) a.add(c[k].a, v[k].h, v[k].l);
     const float2 s = add2(a.S, a.C);
     const float2 e = sub2(a.C, sub2(s, a.S));
     return make_float4(s.x, s.y, e.x, e.y);
@@ -360,19 +388,24 @@ struct RegTile {
       if (live(r) && active) g[toff | roff(r)] = TP::from_sm(v[r]);
   }
 
-  template <int K, bool CTRL>
-  __device__ __forceinline__ void dense1(const Coef* cf, uint32_t lmask, const uint8_t* rexp) {
+  template <int K, bool CTRL, bool REAL>
+  __device__ __forceinline__ void dense1(const Coef* cf, uint32_t lmask) {
     Coef c[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) c[j] = cf[j];
-    (void)rexp;  // 2x2 rows keep TwoSum accumulation (exact under cancellation)
+    // 2x2 rows keep TwoSum accumulation (exact under cancellation).
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (r & (1 << K)) continue;
       if (CTRL && ((toff | roff(r)) & lmask) != lmask) continue;
       const Val x[2] = {TP::val(v[r]), TP::val(v[r | (1 << K)])};
-      v[r] = TP::template mac<2>(c, x);
-      v[r | (1 << K)] = TP::template mac<2>(c + 2, x);
+      if (REAL) {
+        v[r] = TP::template mac_real<2>(c, x);
+        v[r | (1 << K)] = TP::template mac_real<2>(c + 2, x);
+      } else {
+        v[r] = TP::template mac<2>(c, x);
+        v[r | (1 << K)] = TP::template mac<2>(c + 2, x);
+      }
     }
   }
 
@@ -441,11 +474,50 @@ struct RegTile {
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] += ((uint32_t)r & rm) == rp ? g : 0u;
   }
+  // exp(2 pi i g / 2^32) from the table bytes of g (byte `first` up), applied
+  // to the registers r with (r & rm) == rp.
+  __device__ __forceinline__ void apply_group_phase(uint32_t rm, uint32_t rp, uint32_t g, int first,
+                                                    const typename TP::Phase* __restrict__ tab) {
+    Sm z = __ldg(tab + 256 * first + ((g >> (8 * first)) & 255u));
+    for (int b = first + 1; b < 4; ++b) {
+      const Coef c = TP::phase_coef(__ldg(tab + 256 * b + ((g >> (8 * b)) & 255u)));
+      const Val x = TP::val(z);
+      z = TP::template mac<1>(&c, &x);
+    }
+    const Coef cz = TP::phase_coef(z);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (((uint32_t)r & rm) != rp) continue;
+      const Val x = TP::val(v[r]);
+      v[r] = TP::template mac<1>(&cz, &x);
+    }
+  }
   __device__ __forceinline__ void poly(const TileOp* __restrict__ t, uint64_t base,
                                        const typename TP::Phase* __restrict__ tab) {
     const int count = t[0].k;
     const int first = t[0].nloc;
     if (first > 4) return;
+    if (t[0].tpos[0]) {
+      // Factored: each group's phase is one table product per thread,
+      // multiplied into the group's registers.
+      uint32_t g = 0, grm = t[0].tj[0], grp = t[0].tj[1];
+      int gfirst = t[0].tj[2];
+      for (int i = 0;; ++i) {
+        const bool end = i == count;
+        const uint32_t rm = end ? 0u : t[i].tj[0], rp = end ? 0u : t[i].tj[1];
+        if (end || rm != grm || rp != grp) {
+          if (g != 0u) apply_group_phase(grm, grp, g, gfirst, tab);
+          if (end) break;
+          g = 0;
+          grm = rm;
+          grp = rp;
+          gfirst = t[i].tj[2];
+        }
+        if ((base & t[i].gmask) != t[i].gpat) continue;
+        g += (toff & t[i].lmask) == t[i].lpat ? t[i].ptab : 0u;
+      }
+      return;
+    }
     uint32_t acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0u;
@@ -502,6 +574,16 @@ struct RegTile {
   }
 };
 
+template <class RT, bool CTRL, bool REAL>
+__device__ __forceinline__ void dense1_k(RT& rt, int k, const typename RT::Coef* cf, uint32_t lmask) {
+  switch (k) {
+    case 0: rt.template dense1<0, CTRL, REAL>(cf, lmask); break;
+    case 1: rt.template dense1<1, CTRL, REAL>(cf, lmask); break;
+    case 2: if constexpr (RT::RB > 2) rt.template dense1<(RT::RB > 2 ? 2 : 0), CTRL, REAL>(cf, lmask); break;
+    default: if constexpr (RT::RB > 3) rt.template dense1<(RT::RB > 3 ? 3 : 0), CTRL, REAL>(cf, lmask); break;
+  }
+}
+
 template <class RT, int K>
 __device__ __forceinline__ void dense2_k1(RT& rt, int k1, const typename RT::Coef* cf, uint32_t lmask,
                                           const uint8_t* rexp) {
@@ -552,19 +634,11 @@ __device__ __forceinline__ void consume_tile(unsigned char* smem, const TileOp* 
         break;
       case TOP_DENSE1:
         if (op.lmask == 0) {
-          switch (op.tpos[0]) {
-            case 0: rt.template dense1<0, false>(cf, 0, op.tj); break;
-            case 1: rt.template dense1<1, false>(cf, 0, op.tj); break;
-            case 2: if constexpr (RT::RB > 2) rt.template dense1<(RT::RB > 2 ? 2 : 0), false>(cf, 0, op.tj); break;
-            default: if constexpr (RT::RB > 3) rt.template dense1<(RT::RB > 3 ? 3 : 0), false>(cf, 0, op.tj); break;
-          }
+          if (op.nloc) dense1_k<RT, false, true>(rt, op.tpos[0], cf, 0);
+          else dense1_k<RT, false, false>(rt, op.tpos[0], cf, 0);
         } else {
-          switch (op.tpos[0]) {
-            case 0: rt.template dense1<0, true>(cf, op.lmask, op.tj); break;
-            case 1: rt.template dense1<1, true>(cf, op.lmask, op.tj); break;
-            case 2: if constexpr (RT::RB > 2) rt.template dense1<(RT::RB > 2 ? 2 : 0), true>(cf, op.lmask, op.tj); break;
-            default: if constexpr (RT::RB > 3) rt.template dense1<(RT::RB > 3 ? 3 : 0), true>(cf, op.lmask, op.tj); break;
-          }
+          if (op.nloc) dense1_k<RT, true, true>(rt, op.tpos[0], cf, op.lmask);
+          else dense1_k<RT, true, false>(rt, op.tpos[0], cf, op.lmask);
         }
         break;
       case TOP_XSWAP:
