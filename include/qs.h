@@ -175,25 +175,27 @@ typedef struct {
                          qubits above the resident low block that one fused
                          block may span (the block's tile holds 2^max_fuse
                          strided chunks); 0 = the qs_autotune choice for this
-                         dtype, math mode and qubit count (3 if untuned) */
+                         dtype, math mode and qubit count (4 if untuned) */
   int32_t use_graph;  /* 1: capture the launch sequence as a CUDA graph and
                          replay it (the graph is cached per circuit pointer) */
   int32_t reserved[6];
 } qs_run_opts;
 
-/* Run a circuit on one state.  Consecutive gates whose qubits fit one
- * block of at most max_fuse qubits are applied by one fused kernel that
- * keeps the block's amplitudes in shared memory for all of its gates
- * (related work, Sec. I: gate fusion and cache blocking).  Block products
- * needed on the host are composed in FP64.  Result equals applying the
- * gates one by one, up to rounding.  opts may be NULL (autotuned, no graph). */
+/* Run a circuit on one state.  Consecutive gates on the same one or two
+ * qubits are first multiplied into one 2x2 / 4x4 matrix in FP64 where that
+ * saves arithmetic (never for permutations); then gates whose qubits fit
+ * one block of at most max_fuse qubits are applied by one fused kernel that
+ * keeps the block's amplitudes on chip for all of its gates (related work,
+ * Sec. I: gate fusion and cache blocking).  Result equals applying the
+ * gates one by one, up to rounding; permutations and SWAPs move amplitudes
+ * exactly.  opts may be NULL (autotuned, no graph). */
 qs_status qs_fuse_run(qs_state s, const qs_circuit* c, const qs_run_opts* opts);
 
 /* Autotuner for fusion: run circuit c on s with every fusion setting
  * (max_fuse 1..6, which also sets the tile shape: 2^max_fuse strided chunks
  * of contiguous amplitudes), time each on the device, and remember the
  * fastest fused setting for states of s's dtype, math mode and qubit count;
- * qs_fuse_run with max_fuse = 0 then uses it (default 3 before any tuning).
+ * qs_fuse_run with max_fuse = 0 then uses it (default 4 before any tuning).
  * s is scratch: it is reset to |0...0> before each trial and holds the last
  * trial's result afterwards.  Synchronous.  best_max_fuse and best_ms may be
  * NULL. */

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "qs_fuser.h"
+#include "qs_matfuse.h"
 #include "qs_internal.h"
 #include "qs_tile_dev.cuh"
 
@@ -243,6 +244,8 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
     std::vector<FGate> gates;
     gates.reserve((size_t)c->n_gates);
     for (int64_t g = 0; g < c->n_gates; ++g) gates.push_back(normalise(c, c->gates[g]));
+    MatFuser mf;  // fused matrices live until this state's blocks are copied out
+    gates = mf.run(gates);
     bstates[i].psi = s->psi;
     bstates[i].block0 = (uint32_t)blocks.size();
     std::vector<char> taken(gates.size(), 0);

@@ -19,7 +19,7 @@ void release_plan_cache(qs_state s) { release_batch_cache(s); }
 // Fusion width chosen by qs_autotune, per (device, dtype, math, qubits).
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int, int>, int> g_tuned;
-constexpr int kDefaultMaxFuse = 3;
+constexpr int kDefaultMaxFuse = 4;
 
 int fuse_width_for(qs_state s);
 

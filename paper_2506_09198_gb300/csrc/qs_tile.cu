@@ -30,6 +30,7 @@
 #include "qs_tile.cuh"
 #include "qs_tile_dev.cuh"
 #include "qs_fuser.h"
+#include "qs_matfuse.h"
 
 namespace qs {
 
@@ -324,6 +325,8 @@ qs_status run_fused(qs_state s, const qs_circuit* c, int max_high) {
   std::vector<FGate> gates;
   gates.reserve((size_t)c->n_gates);
   for (int64_t i = 0; i < c->n_gates; ++i) gates.push_back(normalise(c, c->gates[i]));
+  MatFuser mf;  // owns the fused matrices until the blocks are launched
+  gates = mf.run(gates);
   if (max_high > kTileMaxHigh) max_high = kTileMaxHigh;
   if (s->dtype == QS_C64) return run_blocks<TileF32>(s, gates, max_high);
   if (s->math == QS_MATH_FP64) return run_blocks<TileF64>(s, gates, max_high);
