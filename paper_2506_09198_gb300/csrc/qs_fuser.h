@@ -497,6 +497,7 @@ inline std::vector<TileOp> schedule_layouts(const std::vector<TileOp>& ops, int 
         }
         run[0].tpos[0] = fact < bytes * R ? 1 : 0;
       }
+      for (TileOp& t : run) t.coef = (uint32_t)t.tj[0] | (uint32_t)t.tj[1] << 8 | (uint32_t)t.tj[2] << 16;
       out.insert(out.end(), run.begin(), run.end());
       i += cnt - 1;
       continue;

@@ -49,6 +49,12 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_tile(typename TP
   const uint32_t n_chunks = 1u << plan.m;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * tile_bytes);
   uint64_t* done = full + kStages;
+  // The block's ops and coefficients, staged once per CTA where the policy
+  // asks for it: every thread reads them for every tile, and shared-memory
+  // vector loads beat constant-bank loads with run-time indices.
+  TileOp* s_ops = reinterpret_cast<TileOp*>(done + kStages);
+  using Coef = typename TP::M::Coef;
+  Coef* s_coefs = reinterpret_cast<Coef*>(s_ops + plan.nops);
   const int tid = threadIdx.x;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -56,6 +62,19 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_tile(typename TP
       mbar_init(&done[s], kTileConsumers);
     }
     mbar_fence_init();
+  }
+  {
+    static_assert(sizeof(TileOp) % 16 == 0 && sizeof(Coef) % 16 == 0, "16-byte staging");
+    if (TP::kStagePlan) {
+      const uint4* so = reinterpret_cast<const uint4*>(plan.ops);
+      uint4* d = reinterpret_cast<uint4*>(s_ops);
+      const int n_op16 = plan.nops * (int)(sizeof(TileOp) / 16);
+      for (int i = tid; i < n_op16; i += blockDim.x) d[i] = so[i];
+      const uint4* sc = reinterpret_cast<const uint4*>(plan.coefs);
+      uint4* dc = reinterpret_cast<uint4*>(s_coefs);
+      const int n_cf16 = plan.ncoefs * (int)(sizeof(Coef) / 16);
+      for (int i = tid; i < n_cf16; i += blockDim.x) dc[i] = sc[i];
+    }
   }
   __syncthreads();
 
@@ -128,7 +147,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_tile(typename TP
     if (consumers_any(!ok)) break;
     Sm* t = reinterpret_cast<Sm*>(smem + (size_t)s * tile_bytes);
     const uint64_t base = tile_base(tau, plan.L, plan.m, plan.base_high);
-    consume_tile<TP>(reinterpret_cast<unsigned char*>(t), plan.ops, plan.nops, plan.coefs, plan.perm,
+    consume_tile<TP>(reinterpret_cast<unsigned char*>(t), TP::kStagePlan ? s_ops : plan.ops, plan.nops,
+                     TP::kStagePlan ? s_coefs : plan.coefs, plan.perm,
                      static_cast<const typename TP::Phase*>(plan.phase_tab), plan.L + plan.m, base, tid);
     fence_async_smem();
     mbar_arrive(&done[s]);
@@ -149,6 +169,10 @@ constexpr int kPermMaxHigh = QS_PERM_MAX_HIGH;  // high qubits of a permutation-
 constexpr int kMinChunkLog128 = 3;  // chunks of at least 128 bytes
 constexpr int kMinChunkLog64 = 4;
 
+static_assert(sizeof(TilePlan<MathDF::Coef>) <= 32764 && sizeof(TilePlan<MathF64::Coef>) <= 32764 &&
+                  sizeof(TilePlan<MathF32::Coef>) <= 32764,
+              "a plan must fit the kernel parameter space");
+
 template <class Coef>
 void fill_plan(TilePlan<Coef>* plan, int n, const BlockOut<Coef>& bo) {
   const Geom& g = bo.geom;
@@ -165,6 +189,7 @@ void fill_plan(TilePlan<Coef>* plan, int n, const BlockOut<Coef>& bo) {
     plan->chunk_off[c] = off;
   }
   plan->nops = (int)bo.ops.size();
+  plan->ncoefs = (int)bo.coefs.size();
   std::memcpy(plan->ops, bo.ops.data(), bo.ops.size() * sizeof(TileOp));
   std::memcpy(plan->coefs, bo.coefs.data(), bo.coefs.size() * sizeof(Coef));
   if (!bo.perm.empty()) std::memcpy(plan->perm, bo.perm.data(), bo.perm.size());
@@ -172,8 +197,10 @@ void fill_plan(TilePlan<Coef>* plan, int n, const BlockOut<Coef>& bo) {
 
 template <class TP>
 qs_status launch_plan(qs_state s, const TilePlan<typename TP::M::Coef>& plan) {
+  using Coef = typename TP::M::Coef;
   const size_t tile_bytes = sizeof(typename TP::Glob) << (plan.L + plan.m);
-  const size_t smem = kStages * tile_bytes + 2 * kStages * sizeof(uint64_t);
+  const size_t smem = kStages * tile_bytes + 2 * kStages * sizeof(uint64_t) +
+                      (TP::kStagePlan ? (size_t)plan.nops * sizeof(TileOp) + (size_t)plan.ncoefs * sizeof(Coef) : 0);
   auto kern = k_tile<TP>;
   // The dynamic shared-memory limit is a property of the function: set it
   // once to the largest tile so that launches with any tile size are valid.
@@ -184,8 +211,8 @@ qs_status launch_plan(qs_state s, const TilePlan<typename TP::M::Coef>& plan) {
   {
     std::lock_guard<std::mutex> lk(mu);
     if (!attr_set) {
-      const size_t max_smem =
-          kStages * ((size_t)sizeof(typename TP::Glob) << TP::kTileLog) + 2 * kStages * sizeof(uint64_t);
+      const size_t max_smem = kStages * ((size_t)sizeof(typename TP::Glob) << TP::kTileLog) +
+                              2 * kStages * sizeof(uint64_t) + kTileMaxOps * sizeof(TileOp) + kTileMaxCoefBytes;
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_tile)");
       attr_set = true;
@@ -251,7 +278,7 @@ qs_status run_blocks(qs_state s, const std::vector<FGate>& gates, int max_high) 
   // Scheduling adds at most one layout change per non-diagonal gate (weight
   // 2 in the op budget; diagonal gates weigh 1), plus one bank-friendly
   // layout before the first op and one after the last.
-  const Limits lim{kTileMaxOps - 2, kTileMaxCoefs, kTileMaxPermBytes};
+  const Limits lim{kTileMaxOps - 2, std::min(kTileMaxCoefs, kTileMaxCoefBytes / (int)sizeof(Coef)), kTileMaxPermBytes};
   const void* ptab = phase_table(s->device, TP::kPhaseFormat);
   if (!ptab) return fail(QS_ERR_CUDA, "phase tables missing on device %d", s->device);
   static thread_local std::vector<unsigned char> plan_mem;

@@ -21,6 +21,9 @@ constexpr int kTileMaxHigh = 8;
 constexpr int kTileMaxChunks = 1 << kTileMaxHigh;
 constexpr int kTileMaxCoefs = 320;
 constexpr int kTileMaxPermBytes = 512;
+// A block's ops and coefficients are staged in shared memory next to the
+// tile ring; this many bytes of coefficients keep two CTAs per SM.
+constexpr int kTileMaxCoefBytes = 10752;
 
 // Inside a tile every consumer thread holds 2^RB amplitudes in registers.
 // A layout names the RB local bits that index a thread's registers (in
@@ -60,7 +63,16 @@ enum TileOpKind : uint8_t {
 
 // Before scheduling (host), dense gates carry local bit positions in tpos;
 // the scheduler rewrites them to register bit indices.
-struct TileOp {
+// 64 bytes, 16-byte aligned: the first 16 bytes hold everything a phase
+// term reads besides its tile predicate (the next 16), so a term is two
+// vector loads.
+struct alignas(16) TileOp {
+  uint32_t lmask;   // local control mask (PHASE/NEG: pattern mask; POLY/TERM: thread bits)
+  uint32_t lpat;    // PHASE/NEG: local pattern (POLY/TERM: thread bits)
+  uint32_t coef;    // first coefficient in the pool; POLY/TERM after scheduling:
+                    // register mask | register pattern << 8 | first byte << 16
+  uint32_t ptab;    // PERM: byte offset of the inverse table; POLY/TERM: m
+  uint64_t gmask, gpat;  // the op acts on a tile iff (base & gmask) == gpat
   uint8_t kind;
   uint8_t k;        // DIAG / PERM: number of targets; LAYOUT: register bits
   uint8_t nloc;     // DIAG: local targets
@@ -68,18 +80,16 @@ struct TileOp {
   uint8_t tpos[8];
   uint8_t tj[8];    // DIAG: sub-register bit of each local target
   uint8_t gq[8];    // DIAG: global qubit of target j when not local, else 0xFF
-  uint32_t lmask;   // local control mask (PHASE/NEG: pattern mask)
-  uint32_t lpat;    // PHASE/NEG: local pattern
-  uint64_t gmask, gpat;  // the op acts on a tile iff (base & gmask) == gpat
-  uint32_t coef;    // first coefficient in the pool
-  uint32_t ptab;    // PERM: byte offset of the inverse table; POLY/TERM: m
+  uint8_t pad[4];
 };
+static_assert(sizeof(TileOp) == 64, "TileOp is 64 bytes");
 
 template <class Coef>
 struct TilePlan {
   int n;
   int L, m;                            // chunk = 2^L amplitudes, 2^m chunks per tile
   int nops;
+  int ncoefs;
   uint64_t n_tiles;
   uint64_t base_high[kTileMaxHigh];    // ~((1 << hq[j]) - 1), ascending: tile base expansion
   uint64_t chunk_off[kTileMaxChunks];  // amplitude offset of chunk c from the base

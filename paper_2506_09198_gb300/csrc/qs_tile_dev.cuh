@@ -101,6 +101,8 @@ __device__ __forceinline__ bool consumers_any(bool v) {
 // ---------------------------------------------------------------------------
 struct TileF32 {
   using M = MathF32;
+  // Stage the block's ops and coefficients in shared memory.
+  static constexpr bool kStagePlan = true;
   using Glob = float2;
   using Sm = float2;
   static constexpr int kTileLog = 12;  // 4096 amplitudes, 32 KB
@@ -149,6 +151,8 @@ __device__ __forceinline__ double dneg(double x) {
 
 struct TileF64 {
   using M = MathF64;
+  // Stage the block's ops and coefficients in shared memory.
+  static constexpr bool kStagePlan = true;
   using Glob = double2;
   using Sm = double2;
   static constexpr int kTileLog = 11;  // 2048 amplitudes, 32 KB
@@ -190,6 +194,9 @@ struct TileF64 {
 // Float-float tile element: (re_h, im_h, re_l, im_l), |l| <= ulp(h)/2.
 struct TileDF {
   using M = MathDF;
+  // The float-float plan stays in the parameter bank: staged in shared
+  // memory, the compiler keeps more of it live and spills.
+  static constexpr bool kStagePlan = false;
   using Glob = double2;
   using Sm = float4;
   static constexpr int kTileLog = 11;
@@ -500,41 +507,42 @@ struct RegTile {
     if (t[0].tpos[0]) {
       // Factored: each group's phase is one table product per thread,
       // multiplied into the group's registers.
-      uint32_t g = 0, grm = t[0].tj[0], grp = t[0].tj[1];
-      int gfirst = t[0].tj[2];
+      uint32_t g = 0, gkey = t[0].coef;
       for (int i = 0;; ++i) {
         const bool end = i == count;
-        const uint32_t rm = end ? 0u : t[i].tj[0], rp = end ? 0u : t[i].tj[1];
-        if (end || rm != grm || rp != grp) {
-          if (g != 0u) apply_group_phase(grm, grp, g, gfirst, tab);
+        uint4 a = make_uint4(0u, 0u, 0u, 0u);
+        ulonglong2 pr = make_ulonglong2(0ull, 0ull);
+        if (!end) {
+          a = *reinterpret_cast<const uint4*>(t + i);  // lmask, lpat, group key, m
+          pr = *reinterpret_cast<const ulonglong2*>(&t[i].gmask);
+        }
+        if (end || a.z != gkey) {
+          if (g != 0u) apply_group_phase(gkey & 0xFFu, (gkey >> 8) & 0xFFu, g, (int)(gkey >> 16) & 0xFF, tab);
           if (end) break;
           g = 0;
-          grm = rm;
-          grp = rp;
-          gfirst = t[i].tj[2];
+          gkey = a.z;
         }
-        if ((base & t[i].gmask) != t[i].gpat) continue;
-        g += (toff & t[i].lmask) == t[i].lpat ? t[i].ptab : 0u;
+        if ((base & pr.x) != pr.y) continue;
+        g += (toff & a.x) == a.y ? a.w : 0u;
       }
       return;
     }
     uint32_t acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0u;
-    uint32_t g = 0, grm = t[0].tj[0], grp = t[0].tj[1];
+    uint32_t g = 0, gkey = t[0].coef;
     for (int i = 0; i < count; ++i) {
-      const TileOp& op = t[i];
-      const uint32_t rm = op.tj[0], rp = op.tj[1];
-      if (rm != grm || rp != grp) {  // uniform: the same plan for every thread
-        add_group(acc, grm, grp, g);
+      const uint4 a = *reinterpret_cast<const uint4*>(t + i);  // lmask, lpat, group key, m
+      const ulonglong2 pr = *reinterpret_cast<const ulonglong2*>(&t[i].gmask);
+      if (a.z != gkey) {  // uniform: the same plan for every thread
+        add_group(acc, gkey & 0xFFu, (gkey >> 8) & 0xFFu, g);
         g = 0;
-        grm = rm;
-        grp = rp;
+        gkey = a.z;
       }
-      if ((base & op.gmask) != op.gpat) continue;
-      g += (toff & op.lmask) == op.lpat ? op.ptab : 0u;
+      if ((base & pr.x) != pr.y) continue;
+      g += (toff & a.x) == a.y ? a.w : 0u;
     }
-    add_group(acc, grm, grp, g);
+    add_group(acc, gkey & 0xFFu, (gkey >> 8) & 0xFFu, g);
     if (first == 4) {
 #pragma unroll
       for (int r = 0; r < R; ++r) v[r] = TP::neg_if(v[r], acc[r] & 0x80000000u);
