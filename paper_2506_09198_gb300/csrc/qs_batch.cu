@@ -36,15 +36,18 @@ constexpr int kBatchLocalMax = 16;
 
 struct BatchBlock {
   int L, m, nops, pad;
-  uint32_t op0, coef0, perm0, pad2;
+  uint32_t op0, coef0, perm0, ncoefs;
   uint64_t n_tiles;
   uint64_t base_high[kTileMaxHigh];
   int8_t hq[kTileMaxHigh];
 };
 
+// A work item: blocks block0 .. block0 + nblocks - 1 of one state, in
+// order; of each block only tiles tau0 .. tau1 - 1 (clamped to its count).
 struct BatchState {
   void* psi;
   uint32_t block0, nblocks;
+  uint64_t tau0, tau1;
 };
 
 struct TileDesc {
@@ -66,6 +69,10 @@ struct BatchArgs {
   uint32_t* err;
 };
 
+// Shared memory for staging one block's plan (as in k_tile: keeps two CTAs
+// per SM next to the tile ring).
+constexpr size_t kStageBytes = kTileMaxOps * sizeof(TileOp) + kTileMaxCoefBytes;
+
 __device__ __forceinline__ uint64_t chunk_offset(const BatchBlock& b, uint32_t c) {
   uint64_t off = 0;
   for (int j = 0; j < b.m; ++j)
@@ -82,6 +89,10 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_batch(const Batc
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kMaxTileBytes);
   uint64_t* done = full + kStages;
   TileDesc* desc = reinterpret_cast<TileDesc*>(done + kStages);
+  // Staging area for the current block's ops and coefficients (policies
+  // that stage, blocks that fit).
+  using Coef = typename TP::M::Coef;
+  TileOp* s_ops = reinterpret_cast<TileOp*>(desc + kStages);
   const int tid = threadIdx.x;
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -136,7 +147,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_batch(const Batc
         const BatchBlock& b = a.blocks[bi];
         const uint32_t chunk_bytes = (uint32_t)sizeof(Glob) << b.L;
         const uint32_t tile_bytes = chunk_bytes << b.m;
-        for (uint64_t tau = 0; tau < b.n_tiles; ++tau, ++j) {
+        const uint64_t tau_end = st.tau1 < b.n_tiles ? st.tau1 : b.n_tiles;
+        for (uint64_t tau = st.tau0; tau < tau_end; ++tau, ++j) {
           const int s = (int)(j % kStages);
           if (!release(s)) {
             ok = false;
@@ -183,6 +195,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_batch(const Batc
   }
 
   // ---------------- consumers ----------------
+  uint32_t staged = 0xFFFFFFFFu;
   for (uint32_t j = 0;; ++j) {
     const int s = (int)(j % kStages);
     const bool ok = mbar_wait(&full[s], (j / kStages) & 1u, a.err);
@@ -190,11 +203,31 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_batch(const Batc
     const TileDesc d = desc[s];
     if (d.block == 0xFFFFFFFFu) break;
     const BatchBlock& b = a.blocks[d.block];
+    const TileOp* ops = a.ops + b.op0;
+    const Coef* coefs = a.coefs + b.coef0;
+    if (TP::kStagePlan && b.nops * sizeof(TileOp) + b.ncoefs * sizeof(Coef) <= kStageBytes) {
+      Coef* s_coefs = reinterpret_cast<Coef*>(s_ops + b.nops);
+      if (d.block != staged) {  // uniform: every consumer reads the same descriptor
+        consumers_sync();       // the previous block's plan is no longer read
+        const uint4* so = reinterpret_cast<const uint4*>(ops);
+        uint4* dst = reinterpret_cast<uint4*>(s_ops);
+        const int n_op16 = b.nops * (int)(sizeof(TileOp) / 16);
+        for (int i = tid; i < n_op16; i += kTileConsumers) dst[i] = so[i];
+        const uint4* sc = reinterpret_cast<const uint4*>(coefs);
+        uint4* dc = reinterpret_cast<uint4*>(s_coefs);
+        const int n_cf16 = (int)(b.ncoefs * sizeof(Coef) / 16);
+        for (int i = tid; i < n_cf16; i += kTileConsumers) dc[i] = sc[i];
+        consumers_sync();
+        staged = d.block;
+      }
+      ops = s_ops;
+      coefs = s_coefs;
+    }
     const uint32_t tile_amps = 1u << (b.L + b.m);
     Sm* t = reinterpret_cast<Sm*>(smem + (size_t)s * kMaxTileBytes);
     const uint64_t base = tile_base(d.tau, b.L, b.m, b.base_high);
-    consume_tile<TP>(reinterpret_cast<unsigned char*>(t), a.ops + b.op0, b.nops, a.coefs + b.coef0,
-                     a.perm + b.perm0, a.phase_tab, b.L + b.m, base, tid);
+    consume_tile<TP>(reinterpret_cast<unsigned char*>(t), ops, b.nops, coefs, a.perm + b.perm0, a.phase_tab,
+                     b.L + b.m, base, tid);
     fence_async_smem();
     mbar_arrive(&done[s]);
   }
@@ -213,7 +246,11 @@ struct BatchCache {
   void* dev = nullptr;
   size_t dev_bytes = 0;
   size_t off_states = 0, off_blocks = 0, off_ops = 0, off_coefs = 0, off_perm = 0, off_counter = 0;
-  uint32_t n_states = 0;
+  uint32_t n_states = 0;  // work items of the persistent launch (single-tile states)
+  // Multi-tile states run in steps: step k applies block k of each of them,
+  // its tiles spread over the grid as separate work items (one launch each).
+  std::vector<size_t> step_off;
+  std::vector<uint32_t> step_n;
   cudaGraphExec_t graph = nullptr;
   int grid = 0;
   size_t smem = 0;
@@ -248,6 +285,8 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
     gates = mf.run(gates);
     bstates[i].psi = s->psi;
     bstates[i].block0 = (uint32_t)blocks.size();
+    bstates[i].tau0 = 0;
+    bstates[i].tau1 = ~0ull;
     std::vector<char> taken(gates.size(), 0);
     size_t next = 0;
     while (next < gates.size()) {
@@ -277,6 +316,7 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
       b.nops = (int)bo.ops.size();
       b.op0 = (uint32_t)ops.size();
       b.coef0 = (uint32_t)coefs.size();
+      b.ncoefs = (uint32_t)bo.coefs.size();
       b.perm0 = (uint32_t)perm.size();
       b.n_tiles = 1ull << (s->n - geom.L - geom.m);
       for (int jq = 0; jq < geom.m; ++jq) {
@@ -291,16 +331,59 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
     }
     bstates[i].nblocks = (uint32_t)blocks.size() - bstates[i].block0;
   }
-  // Largest estimated cost first.
-  std::vector<int> order(count);
-  std::iota(order.begin(), order.end(), 0);
+  // States that fit one tile run whole, one CTA each, largest estimated cost
+  // first.  A state of several tiles would serialise all its blocks on one
+  // CTA; instead step k applies block k of every such state, with its tiles
+  // spread over the grid (one launch per step; the launch boundary orders
+  // the blocks of a state).
+  std::vector<int> order;
+  std::vector<int> multi;
+  for (int i = 0; i < count; ++i) {
+    bool one_tile = true;
+    for (uint32_t k = 0; k < bstates[i].nblocks; ++k) one_tile = one_tile && blocks[bstates[i].block0 + k].n_tiles == 1;
+    (one_tile ? order : multi).push_back(i);
+  }
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-  std::vector<BatchState> sorted(count);
-  for (int i = 0; i < count; ++i) sorted[i] = bstates[order[i]];
+  std::vector<BatchState> sorted;
+  for (int i : order) sorted.push_back(bstates[i]);
+  uint32_t nsteps = 0;
+  for (int i : multi) nsteps = std::max(nsteps, bstates[i].nblocks);
+  const uint64_t grid_est = (uint64_t)sm_count(states[0]->device) * kTileMinCtas;
+  std::vector<BatchState> step_items;
+  std::vector<size_t> step_first(nsteps), step_count(nsteps);
+  for (uint32_t k = 0; k < nsteps; ++k) {
+    std::vector<int> here;
+    uint64_t total = 0;
+    for (int i : multi)
+      if (bstates[i].nblocks > k) {
+        here.push_back(i);
+        total += blocks[bstates[i].block0 + k].n_tiles;
+      }
+    std::stable_sort(here.begin(), here.end(), [&](int x, int y) {
+      return blocks[bstates[x].block0 + k].n_tiles > blocks[bstates[y].block0 + k].n_tiles;
+    });
+    // Tiles per work item: about two items per CTA.
+    const uint64_t per = std::max<uint64_t>(1, (total + 2 * grid_est - 1) / (2 * grid_est));
+    step_first[k] = step_items.size();
+    for (int i : here) {
+      const uint64_t nt = blocks[bstates[i].block0 + k].n_tiles;
+      for (uint64_t t0 = 0; t0 < nt; t0 += per) {
+        BatchState w = bstates[i];
+        w.block0 = bstates[i].block0 + k;
+        w.nblocks = 1;
+        w.tau0 = t0;
+        w.tau1 = std::min(nt, t0 + per);
+        step_items.push_back(w);
+      }
+    }
+    step_count[k] = step_items.size() - step_first[k];
+  }
 
   size_t off = 0;
   bc->off_states = off;
   off = align_up(off + sorted.size() * sizeof(BatchState), 256);
+  const size_t off_steps = off;
+  off = align_up(off + step_items.size() * sizeof(BatchState), 256);
   bc->off_blocks = off;
   off = align_up(off + blocks.size() * sizeof(BatchBlock), 256);
   bc->off_ops = off;
@@ -310,7 +393,7 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
   bc->off_perm = off;
   off = align_up(off + perm.size() + 1, 256);
   bc->off_counter = off;
-  off = align_up(off + sizeof(uint32_t), 256);
+  off = align_up(off + (1 + (size_t)nsteps) * sizeof(uint32_t), 256);
   if (bc->dev_bytes < off) {
     if (bc->dev) {
       cudaStreamSynchronize(states[0]->stream);
@@ -323,43 +406,58 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
   }
   std::vector<unsigned char> host(off, 0);
   std::memcpy(host.data() + bc->off_states, sorted.data(), sorted.size() * sizeof(BatchState));
+  if (!step_items.empty())
+    std::memcpy(host.data() + off_steps, step_items.data(), step_items.size() * sizeof(BatchState));
   std::memcpy(host.data() + bc->off_blocks, blocks.data(), blocks.size() * sizeof(BatchBlock));
   std::memcpy(host.data() + bc->off_ops, ops.data(), ops.size() * sizeof(TileOp));
   std::memcpy(host.data() + bc->off_coefs, coefs.data(), coefs.size() * sizeof(Coef));
   if (!perm.empty()) std::memcpy(host.data() + bc->off_perm, perm.data(), perm.size());
   // Stream-ordered after the previous batch that used this buffer.
   QS_CUDA(cudaMemcpyAsync(bc->dev, host.data(), off, cudaMemcpyHostToDevice, states[0]->stream));
-  bc->n_states = (uint32_t)count;
+  bc->n_states = (uint32_t)sorted.size();
+  bc->step_off.resize(nsteps);
+  bc->step_n.resize(nsteps);
+  for (uint32_t k = 0; k < nsteps; ++k) {
+    bc->step_off[k] = off_steps + step_first[k] * sizeof(BatchState);
+    bc->step_n[k] = (uint32_t)step_count[k];
+  }
   return QS_OK;
 }
 
 template <class TP>
 qs_status launch_batch(qs_state s0, BatchCache* bc, cudaStream_t stream) {
   const size_t smem = kStages * ((size_t)sizeof(typename TP::Glob) << TP::kTileLog) + 2 * kStages * sizeof(uint64_t) +
-                      kStages * sizeof(TileDesc);
+                      kStages * sizeof(TileDesc) + (TP::kStagePlan ? kStageBytes : 0);
   auto kern = k_batch<TP>;
   QS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTileThreads, smem) != cudaSuccess || occ < 1) occ = 1;
-  int grid = sm_count(s0->device) * occ;
-  if ((uint32_t)grid > bc->n_states) grid = (int)bc->n_states;
+  const uint32_t full = (uint32_t)(sm_count(s0->device) * occ);
   BatchArgs<TP> args;
   unsigned char* base = (unsigned char*)bc->dev;
-  args.states = (const BatchState*)(base + bc->off_states);
   args.blocks = (const BatchBlock*)(base + bc->off_blocks);
   args.ops = (const TileOp*)(base + bc->off_ops);
   args.coefs = (const typename TP::M::Coef*)(base + bc->off_coefs);
   args.perm = base + bc->off_perm;
   args.phase_tab = static_cast<const typename TP::Phase*>(phase_table(s0->device, TP::kPhaseFormat));
   if (!args.phase_tab) return fail(QS_ERR_CUDA, "phase tables missing on device %d", s0->device);
-  args.n_states = bc->n_states;
-  args.counter = (uint32_t*)(base + bc->off_counter);
+  uint32_t* counters = (uint32_t*)(base + bc->off_counter);
   args.err = device_error_word(s0->device);
   if (!args.err) return fail(QS_ERR_CUDA, "device error word unavailable");
-  QS_CUDA(cudaMemsetAsync(args.counter, 0, sizeof(uint32_t), stream));
-  kern<<<grid, kTileThreads, smem, stream>>>(args);
-  QS_CUDA(cudaGetLastError());
-  return QS_OK;
+  QS_CUDA(cudaMemsetAsync(counters, 0, (1 + bc->step_n.size()) * sizeof(uint32_t), stream));
+  auto go = [&](const BatchState* items, uint32_t n, uint32_t* counter) -> qs_status {
+    if (n == 0) return QS_OK;
+    args.states = items;
+    args.n_states = n;
+    args.counter = counter;
+    kern<<<std::min(full, n), kTileThreads, smem, stream>>>(args);
+    QS_CUDA(cudaGetLastError());
+    return QS_OK;
+  };
+  qs_status st = go((const BatchState*)(base + bc->off_states), bc->n_states, counters);
+  for (size_t k = 0; k < bc->step_n.size() && st == QS_OK; ++k)
+    st = go((const BatchState*)(base + bc->step_off[k]), bc->step_n[k], counters + 1 + k);
+  return st;
 }
 
 template <class TP>
@@ -406,6 +504,8 @@ qs_status run_batch(qs_state* states, const qs_circuit* const* circuits, int cou
     if (st != QS_OK) return st;
   } else {
     bc->n_states = 0;
+    bc->step_off.clear();
+    bc->step_n.clear();
   }
   bc->key = key;
   bc->dtype = (int)s0->dtype;
@@ -414,7 +514,7 @@ qs_status run_batch(qs_state* states, const qs_circuit* const* circuits, int cou
   for (int i = 1; i < count; ++i)
     if (states[i]->stream != s0->stream) QS_CUDA(cudaStreamSynchronize(states[i]->stream));
   auto enqueue = [&](cudaStream_t stream) -> qs_status {
-    if (bc->n_states > 0) {
+    if (bc->n_states > 0 || !bc->step_n.empty()) {
       qs_status r = launch_batch<TP>(s0, bc, stream);
       if (r != QS_OK) return r;
     }

@@ -96,8 +96,14 @@ static int row_exponent(const double* U, int row, int dim) {
 
 constexpr int kThreads = 256;
 
+#ifdef QS_DENSE1_MIN_BLOCKS
+#define QS_DENSE1_BOUNDS __launch_bounds__(kThreads, QS_DENSE1_MIN_BLOCKS)
+#else
+#define QS_DENSE1_BOUNDS __launch_bounds__(kThreads)
+#endif
+
 template <class P, int ILP>
-__global__ void __launch_bounds__(kThreads) k_dense1(typename P::Amp* __restrict__ psi, uint64_t n_items,
+__global__ void QS_DENSE1_BOUNDS k_dense1(typename P::Amp* __restrict__ psi, uint64_t n_items,
                                                      uint64_t tbit, DevInsert ins, Mat2<P> g) {
   using Amp = typename P::Amp;
   using Val = typename P::Val;
@@ -126,8 +132,18 @@ __global__ void __launch_bounds__(kThreads) k_dense1(typename P::Amp* __restrict
   }
 }
 
+#ifndef QS_DENSE2_ILP
+#define QS_DENSE2_ILP 1
+#endif
+// Six resident CTAs per SM (40 registers): the float-float 4x4 kernel waits on
+// memory, and the extra warps keep more loads in flight.
+#ifndef QS_DENSE2_MIN_BLOCKS
+#define QS_DENSE2_MIN_BLOCKS 6
+#endif
+#define QS_DENSE2_BOUNDS __launch_bounds__(kThreads, QS_DENSE2_MIN_BLOCKS)
+
 template <class P, int ILP>
-__global__ void __launch_bounds__(kThreads) k_dense2(typename P::Amp* __restrict__ psi, uint64_t n_items,
+__global__ void QS_DENSE2_BOUNDS k_dense2(typename P::Amp* __restrict__ psi, uint64_t n_items,
                                                      uint64_t b0, uint64_t b1, DevInsert ins, Mat4<P> g) {
   using Amp = typename P::Amp;
   using Val = typename P::Val;
@@ -382,7 +398,7 @@ qs_status launch_dense1(qs_state s, int target, uint64_t ctrl_mask, const double
 
 template <class P>
 static qs_status dense2_impl(qs_state s, int t0, int t1, uint64_t ctrl_mask, const double* U) {
-  constexpr int ILP = 1;
+  constexpr int ILP = QS_DENSE2_ILP;
   const uint64_t items = 1ull << (s->n - 2 - popcount64(ctrl_mask));
   DevInsert ins = to_dev(make_insert(with_ctrls({t0, t1}, ctrl_mask), ctrl_mask));
   Mat4<P> g;

@@ -74,7 +74,7 @@ __device__ __forceinline__ void d2ff(double x, float& h, float& l) {
 struct MathF64 {
   using Amp = double2;
   struct Val { double re, im; };
-  struct alignas(16) Coef { double re, im; };
+  struct Coef { double re, im; };
   static __host__ Coef make_coef(double re, double im) { return Coef{re, im}; }
   static __device__ __forceinline__ Val load(const Amp& a) { return Val{a.x, a.y}; }
   static __device__ __forceinline__ Amp pack(const Val& v) { return make_double2(v.re, v.im); }
@@ -160,7 +160,7 @@ struct MathF32 {
   struct Val {
     float2 v, vs;  // (re, im) and (im, re)
   };
-  struct alignas(16) Coef {
+  struct alignas(16) Coef {  // 16-byte aligned: one vector load from a staged pool
     float2 a, b;   // (mr, mr) and (-mi, mi)
   };
   static __host__ Coef make_coef(double re, double im) {
@@ -217,7 +217,7 @@ struct MathDF {
     float2 h, l;    // (re, im) heads and tails
     float2 hs, ls;  // the same, channels swapped (im, re)
   };
-  struct alignas(16) Coef {
+  struct Coef {
     DF2Term a, b;   // A term (mr, mr) and B term (-mi, mi)
   };
   static __host__ Coef make_coef(double re, double im) {
