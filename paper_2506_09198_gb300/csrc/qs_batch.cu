@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_batch(const Batc
     const uint32_t tile_amps = 1u << (b.L + b.m);
     Sm* t = reinterpret_cast<Sm*>(smem + (size_t)s * kMaxTileBytes);
     const uint64_t base = tile_base(d.tau, b.L, b.m, b.base_high);
-    consume_tile<TP>(reinterpret_cast<unsigned char*>(t), ops, b.nops, coefs, a.perm + b.perm0, a.phase_tab,
+    consume_tile<TP>(reinterpret_cast<unsigned char*>(t), ops, b.nops, coefs, a.perm + b.perm0, 0, a.phase_tab,
                      b.L + b.m, base, tid);
     fence_async_smem();
     mbar_arrive(&done[s]);

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_tile(typename TP
     Sm* t = reinterpret_cast<Sm*>(smem + (size_t)s * tile_bytes);
     const uint64_t base = tile_base(tau, plan.L, plan.m, plan.base_high);
     consume_tile<TP>(reinterpret_cast<unsigned char*>(t), TP::kStagePlan ? s_ops : plan.ops, plan.nops,
-                     TP::kStagePlan ? s_coefs : plan.coefs, plan.perm,
+                     TP::kStagePlan ? s_coefs : plan.coefs, plan.perm, plan.fmt,
                      static_cast<const typename TP::Phase*>(plan.phase_tab), plan.L + plan.m, base, tid);
     fence_async_smem();
     mbar_arrive(&done[s]);
@@ -190,6 +190,7 @@ void fill_plan(TilePlan<Coef>* plan, int n, const BlockOut<Coef>& bo) {
   }
   plan->nops = (int)bo.ops.size();
   plan->ncoefs = (int)bo.coefs.size();
+  plan->fmt = 0;
   std::memcpy(plan->ops, bo.ops.data(), bo.ops.size() * sizeof(TileOp));
   std::memcpy(plan->coefs, bo.coefs.data(), bo.coefs.size() * sizeof(Coef));
   if (!bo.perm.empty()) std::memcpy(plan->perm, bo.perm.data(), bo.perm.size());
@@ -273,6 +274,10 @@ qs_status launch_block(qs_state s, const std::vector<FGate>& gates, const std::v
 template <class TP>
 qs_status run_blocks(qs_state s, const std::vector<FGate>& gates, int max_high) {
   using Coef = typename TP::M::Coef;
+  // Float-float blocks that follow one another keep the state in head +
+  // tail float form in HBM between them (16 bytes per amplitude, like the
+  // doubles): only the first reads doubles and only the last writes them.
+  constexpr bool kChain = std::is_same<TP, TileDF>::value;
   const int n = s->n;
   const int min_chunk = sizeof(typename TP::Glob) == 16 ? kMinChunkLog128 : kMinChunkLog64;
   // Scheduling adds at most one layout change per non-diagonal gate (weight
@@ -281,9 +286,20 @@ qs_status run_blocks(qs_state s, const std::vector<FGate>& gates, int max_high) 
   const Limits lim{kTileMaxOps - 2, std::min(kTileMaxCoefs, kTileMaxCoefBytes / (int)sizeof(Coef)), kTileMaxPermBytes};
   const void* ptab = phase_table(s->device, TP::kPhaseFormat);
   if (!ptab) return fail(QS_ERR_CUDA, "phase tables missing on device %d", s->device);
-  static thread_local std::vector<unsigned char> plan_mem;
-  plan_mem.resize(sizeof(TilePlan<Coef>));
-  TilePlan<Coef>* plan = reinterpret_cast<TilePlan<Coef>*>(plan_mem.data());
+  static thread_local std::vector<unsigned char> plan_mem[2];
+  plan_mem[0].resize(sizeof(TilePlan<Coef>));
+  plan_mem[1].resize(sizeof(TilePlan<Coef>));
+  TilePlan<Coef>* plan = reinterpret_cast<TilePlan<Coef>*>(plan_mem[0].data());
+  TilePlan<Coef>* pend = reinterpret_cast<TilePlan<Coef>*>(plan_mem[1].data());
+  bool pend_valid = false;
+  // Launch the held plan; its output stays in float-float form when the
+  // next launch is a float-float plan too.
+  auto flush = [&](bool next_chained) -> qs_status {
+    if (!pend_valid) return QS_OK;
+    pend_valid = false;
+    if (next_chained) pend->fmt |= kTileOutFF;
+    return launch_plan<TP>(s, *pend);
+  };
   BlockOut<Coef> bo;
   std::vector<char> taken(gates.size(), 0);
   size_t next = 0;
@@ -304,46 +320,47 @@ qs_status run_blocks(qs_state s, const std::vector<FGate>& gates, int max_high) 
       members = choose_block(gates, taken, next, n, TP::kTileLog, max_high, min_chunk, lim, 512, &geom);
     // A gate that fits no tile, or a block of one gate (staging gains
     // nothing), runs on the per-gate kernels.
-    if (members.size() <= 1) {
-      qs_status st = dispatch_single(s, gates[next]);
-      if (st != QS_OK) return st;
-      taken[next] = 1;
-      continue;
-    }
-    PlanBuilder<typename TP::M> pb(&bo, geom, lim);
     size_t emitted = 0;
-    for (size_t idx : members) {
-      if (!pb.add(gates[idx])) break;
-      taken[idx] = 1;
-      ++emitted;
+    if (members.size() > 1) {
+      PlanBuilder<typename TP::M> pb(&bo, geom, lim);
+      for (size_t idx : members) {
+        if (!pb.add(gates[idx])) break;
+        taken[idx] = 1;
+        ++emitted;
+      }
     }
     if (emitted == 0) {
-      qs_status st = dispatch_single(s, gates[next]);
+      qs_status st = flush(false);
+      if (st == QS_OK) st = dispatch_single(s, gates[next]);
       if (st != QS_OK) return st;
       taken[next] = 1;
       continue;
     }
-    if (!bo.ops.empty()) {
-      group_terms(bo.ops);
-      bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits, TP::kBankBits);
-      if (bo.ops.size() > (size_t)kTileMaxOps)
-        return fail(QS_ERR_UNSUPPORTED, "fused block of %zu ops exceeds %d", bo.ops.size(), kTileMaxOps);
-      qs_status st;
-      if (std::is_same<TP, TileDF>::value && moves_only(bo.ops)) {
-        // Moves and sign flips are exact in any policy: the FP64 tile skips
-        // the float-float conversions (same tile size and layouts).
-        static_assert(TileF64::kTileLog == TileDF::kTileLog && TileF64::kRegBits == TileDF::kRegBits,
-                      "move-only blocks reuse the float-float geometry");
-        st = launch_block<TileF64>(s, gates, members, emitted, geom, lim);
-      } else {
-        fill_plan(plan, n, bo);
-        plan->phase_tab = ptab;
-        st = launch_plan<TP>(s, *plan);
-      }
+    if (bo.ops.empty()) continue;
+    group_terms(bo.ops);
+    bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits, TP::kBankBits);
+    if (bo.ops.size() > (size_t)kTileMaxOps)
+      return fail(QS_ERR_UNSUPPORTED, "fused block of %zu ops exceeds %d", bo.ops.size(), kTileMaxOps);
+    if (kChain && !pend_valid && moves_only(bo.ops)) {
+      // Moves and sign flips are exact in any policy: outside a float-float
+      // chain the FP64 tile skips the conversions (same tile size and
+      // layouts).
+      static_assert(TileF64::kTileLog == TileDF::kTileLog && TileF64::kRegBits == TileDF::kRegBits,
+                    "move-only blocks reuse the float-float geometry");
+      qs_status st = launch_block<TileF64>(s, gates, members, emitted, geom, lim);
       if (st != QS_OK) return st;
+      continue;
     }
+    fill_plan(plan, n, bo);
+    plan->phase_tab = ptab;
+    const bool chained = kChain && pend_valid;
+    qs_status st = flush(kChain);
+    if (st != QS_OK) return st;
+    if (chained) plan->fmt |= kTileInFF;
+    std::swap(plan, pend);
+    pend_valid = true;
   }
-  return QS_OK;
+  return flush(false);
 }
 
 }  // namespace

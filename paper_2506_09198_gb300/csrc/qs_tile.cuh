@@ -90,6 +90,7 @@ struct TilePlan {
   int L, m;                            // chunk = 2^L amplitudes, 2^m chunks per tile
   int nops;
   int ncoefs;
+  int fmt;                             // kTileInFF | kTileOutFF: float-float tiles in HBM
   uint64_t n_tiles;
   uint64_t base_high[kTileMaxHigh];    // ~((1 << hq[j]) - 1), ascending: tile base expansion
   uint64_t chunk_off[kTileMaxChunks];  // amplitude offset of chunk c from the base
@@ -98,6 +99,12 @@ struct TilePlan {
   uint8_t perm[kTileMaxPermBytes];
   const void* phase_tab;               // exp(2 pi i v 2^(8b) / 2^32) at [256 b + v], the policy's format
 };
+
+// Tile storage in HBM between consecutive float-float blocks: the plan's
+// input and/or output tile holds (re head, im head, re tail, im tail)
+// floats instead of (re, im) doubles.
+constexpr int kTileInFF = 1;
+constexpr int kTileOutFF = 2;
 
 // Phase terms: runs shorter than this stay single phase ops; a run holds at
 // most 255 terms (its count is a byte).

@@ -372,11 +372,13 @@ struct RegTile {
     return o;
   }
 
-  __device__ __forceinline__ void read_glob(const unsigned char* smem) {
+  // raw: the staged tile already holds the working format.
+  __device__ __forceinline__ void read_glob(const unsigned char* smem, bool raw) {
     const Glob* g = reinterpret_cast<const Glob*>(smem);
+    const Sm* t = reinterpret_cast<const Sm*>(smem);
 #pragma unroll
     for (int r = 0; r < R; ++r)
-      if (live(r) && active) v[r] = TP::to_sm(g[toff | roff(r)]);
+      if (live(r) && active) v[r] = raw ? t[toff | roff(r)] : TP::to_sm(g[toff | roff(r)]);
   }
   __device__ __forceinline__ void read_sm(const unsigned char* smem) {
 #pragma unroll
@@ -388,11 +390,15 @@ struct RegTile {
     for (int r = 0; r < R; ++r)
       if (live(r) && active) *reinterpret_cast<Sm*>(smem + sw_off(r)) = v[r];
   }
-  __device__ __forceinline__ void write_glob(unsigned char* smem) const {
+  __device__ __forceinline__ void write_glob(unsigned char* smem, bool raw) const {
     Glob* g = reinterpret_cast<Glob*>(smem);
+    Sm* t = reinterpret_cast<Sm*>(smem);
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-      if (live(r) && active) g[toff | roff(r)] = TP::from_sm(v[r]);
+    for (int r = 0; r < R; ++r) {
+      if (!live(r) || !active) continue;
+      if (raw) t[toff | roff(r)] = v[r];
+      else g[toff | roff(r)] = TP::from_sm(v[r]);
+    }
   }
 
   template <int K, bool CTRL, bool REAL>
@@ -609,7 +615,7 @@ __device__ __forceinline__ void dense2_k1(RT& rt, int k1, const typename RT::Coe
 template <class TP>
 __device__ __forceinline__ void consume_tile(unsigned char* smem, const TileOp* __restrict__ ops, int nops,
                                              const typename TP::M::Coef* __restrict__ coefs,
-                                             const uint8_t* __restrict__ perm_tables,
+                                             const uint8_t* __restrict__ perm_tables, int fmt,
                                              const typename TP::Phase* __restrict__ phase_tab, int tile_log,
                                              uint64_t base, int tid) {
   using RT = RegTile<TP>;
@@ -630,7 +636,7 @@ __device__ __forceinline__ void consume_tile(unsigned char* smem, const TileOp* 
       case TOP_LAYOUT:
         if (first) {
           rt.set_layout(op.tpos, rb, tile_log, tid);
-          rt.read_glob(smem);
+          rt.read_glob(smem, (fmt & kTileInFF) != 0);
           first = false;
         } else {
           consumers_sync();
@@ -686,7 +692,7 @@ __device__ __forceinline__ void consume_tile(unsigned char* smem, const TileOp* 
     }
   }
   consumers_sync();
-  rt.write_glob(smem);
+  rt.write_glob(smem, (fmt & kTileOutFF) != 0);
 }
 
 }  // namespace qs
