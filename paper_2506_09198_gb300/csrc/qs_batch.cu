@@ -18,6 +18,7 @@
 #include <map>
 #include <mutex>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "qs_fuser.h"
@@ -35,7 +36,7 @@ int fuse_width_for(qs_state s);                                              // 
 constexpr int kBatchLocalMax = 16;
 
 struct BatchBlock {
-  int L, m, nops, pad;
+  int L, m, nops, fmt;  // fmt: kTileInFF / kTileOutFF (float-float state between a state's blocks)
   uint32_t op0, coef0, perm0, ncoefs;
   uint64_t n_tiles;
   uint64_t base_high[kTileMaxHigh];
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_batch(const Batc
     const uint32_t tile_amps = 1u << (b.L + b.m);
     Sm* t = reinterpret_cast<Sm*>(smem + (size_t)s * kMaxTileBytes);
     const uint64_t base = tile_base(d.tau, b.L, b.m, b.base_high);
-    consume_tile<TP>(reinterpret_cast<unsigned char*>(t), ops, b.nops, coefs, a.perm + b.perm0, 0, a.phase_tab,
+    consume_tile<TP>(reinterpret_cast<unsigned char*>(t), ops, b.nops, coefs, a.perm + b.perm0, b.fmt, a.phase_tab,
                      b.L + b.m, base, tid);
     fence_async_smem();
     mbar_arrive(&done[s]);
@@ -330,6 +331,12 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
       cost[i] += (double)(1ull << s->n) * (2.0 + (double)b.nops);
     }
     bstates[i].nblocks = (uint32_t)blocks.size() - bstates[i].block0;
+    // Float-float policies keep the state in (head, tail) form between its
+    // blocks: the first block reads doubles, the last writes them.
+    if (std::is_same<TP, TileDF>::value)
+      for (uint32_t k = 0; k < bstates[i].nblocks; ++k)
+        blocks[bstates[i].block0 + k].fmt =
+            (k > 0 ? kTileInFF : 0) | (k + 1 < bstates[i].nblocks ? kTileOutFF : 0);
   }
   // States that fit one tile run whole, one CTA each, largest estimated cost
   // first.  A state of several tiles would serialise all its blocks on one
