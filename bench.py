@@ -354,6 +354,26 @@ def run_extra_workload(args):
 
 
 # ---------------------------------------------------------------------------
+# Multi-rank aggregation (replicas: each rank simulates its own state)
+# ---------------------------------------------------------------------------
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """The slowest rank's time: every rank gets the maximum of all ranks'."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(bytes_per_step: float, steps: int, ms: float, world: int) -> float:
+    """Whole-job GB/s: the units all ranks processed over the slowest rank's time."""
+    return world * bytes_per_step * steps / (ms * 1e-3) / 1e9
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -426,15 +446,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier()
-    ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(t_start.elapsed_time(t_end), world, device="cuda")
     bytes_step = len(gates) * gate_bytes(n, amp_bytes)
-    value = world * bytes_step * args.steps / (ms * 1e-3) / 1e9
+    value = job_throughput(bytes_step, args.steps, ms, world)
 
     # Per-kernel averages over the timed region.
     per_kind = {}

@@ -61,18 +61,14 @@ class _Active:
     stream: object = None
 
 
-class BuddyArena:
-    """Power-of-two sub-allocator over one device allocation (state sizes
-    are powers of two, so a freed state's block merges back with its buddy).
-    Host-side bookkeeping only; the memory is one torch uint8 tensor."""
+class BuddyAllocator:
+    """Power-of-two sub-allocation bookkeeping (state sizes are powers of
+    two, so a freed state's block merges back with its buddy).  Offsets
+    only; BuddyArena puts device memory under it."""
 
     def __init__(self, total_bytes: int, min_bytes: int = 1 << 12):
-        import torch
-
         self.top = max(int(total_bytes).bit_length() - 1, min_bytes.bit_length() - 1)
         self.min_order = min_bytes.bit_length() - 1
-        self.tensor = torch.empty(1 << self.top, dtype=torch.uint8, device="cuda")
-        self.base = self.tensor.data_ptr()
         self.free = {o: set() for o in range(self.min_order, self.top + 1)}
         self.free[self.top].add(0)
 
@@ -104,6 +100,17 @@ class BuddyArena:
             off = min(off, buddy)
             o += 1
         self.free[o].add(off)
+
+
+class BuddyArena(BuddyAllocator):
+    """BuddyAllocator over one device allocation (a torch uint8 tensor)."""
+
+    def __init__(self, total_bytes: int, min_bytes: int = 1 << 12):
+        import torch
+
+        super().__init__(total_bytes, min_bytes)
+        self.tensor = torch.empty(1 << self.top, dtype=torch.uint8, device="cuda")
+        self.base = self.tensor.data_ptr()
 
 
 class Server:

@@ -1,0 +1,142 @@
+"""Host-side logic that needs no GPU: the serving loop's buddy arena and
+request mix, circuit marshalling into the C ABI's records, and the bench's
+aggregation over ranks (world size 2 over gloo on the CPU)."""
+import ctypes
+import math
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def serving():
+    pytest.importorskip("torch")
+    from paper_2506_09198_gb300 import serving as S
+
+    return S
+
+
+def test_buddy_allocator_splits_and_merges():
+    S = serving()
+    a = S.BuddyAllocator(1 << 20)
+    blocks = [a.alloc(1 << 16) for _ in range(16)]
+    assert None not in blocks and len(set(blocks)) == 16
+    assert all(b % (1 << 16) == 0 and 0 <= b < (1 << 20) for b in blocks)
+    assert a.alloc(1 << 12) is None  # full
+    for b in blocks[::2]:
+        a.release(b, 1 << 16)
+    assert a.alloc(1 << 17) is None  # free space is fragmented into 64 KiB holes
+    for b in blocks[1::2]:
+        a.release(b, 1 << 16)
+    assert a.alloc(1 << 20) == 0  # everything merged back
+
+
+def test_buddy_allocator_rounds_up_and_aligns():
+    S = serving()
+    a = S.BuddyAllocator(1 << 20)
+    x = a.alloc(3000)  # rounds up to 4096
+    y = a.alloc(4096)
+    assert x is not None and y is not None and abs(x - y) >= 4096
+    assert x % 4096 == 0 and y % 4096 == 0
+
+
+def test_request_mix_and_sizes():
+    S = serving()
+    reqs = S.make_requests(400, seed=11, n_min=12, n_max=24, rate=50.0)
+    kinds = [r.kind for r in reqs]
+    assert abs(kinds.count("rqc") / 400 - 0.4) < 0.08
+    assert abs(kinds.count("qft") / 400 - 0.3) < 0.08
+    assert abs(kinds.count("grover") / 400 - 0.3) < 0.08
+    ns = np.array([r.n for r in reqs])
+    assert ns.min() >= 12 and ns.max() <= 24
+    # log-uniform: the median sits near sqrt(12 * 24), below the midpoint 18
+    assert 15 <= np.median(ns) <= 18
+    arrivals = np.array([r.arrival for r in reqs])
+    assert np.all(np.diff(arrivals) >= 0)
+    assert abs(arrivals[-1] / 400 - 1 / 50.0) < 0.01  # Poisson rate 50/s
+    for r in reqs:
+        if r.kind == "grover":
+            assert sum(1 for g in r.gates if g.name == "mcz") <= 2 * 16  # iterations capped at 16
+
+
+def test_circuit_marshalling_records():
+    pytest.importorskip("torch")
+    try:
+        from paper_2506_09198_gb300 import qs
+    except ImportError:
+        pytest.skip("libqs not built")
+    rng = W.rng_for(5)
+    gates = [W.H(3), W.CNOT(1, 4), W.gk((0, 2), W.haar_unitary(4, rng), ctrls=(5,)),
+             W.gperm((1, 2, 3), rng.permutation(8).astype(np.uint32)), W.gdiag((4,), [1, -1]), W.SWAP(0, 6)]
+    c = qs.Circuit(gates)
+    assert c.n_gates == len(gates) and c.c.n_gates == len(gates)
+    d_off = p_off = 0
+    for i, g in enumerate(gates):
+        rec = c.gates[i]
+        assert rec.kind == qs._KIND[g.kind]
+        assert rec.k == len(g.targets) and list(rec.targets)[:rec.k] == list(g.targets)
+        assert rec.ctrl_mask == sum(1 << q for q in g.ctrls)
+        if g.kind == "perm":
+            assert rec.offset == p_off
+            assert np.array_equal(c.perm[p_off:p_off + len(g.data)], g.data)
+            p_off += len(g.data)
+        else:
+            flat = np.asarray(g.data, dtype=np.complex128).reshape(-1)
+            assert rec.offset == d_off
+            assert np.array_equal(c.data[d_off:d_off + 2 * flat.size].view(np.complex128), flat)
+            d_off += 2 * flat.size
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, times, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms = bench.max_over_ranks(times[rank], world)
+    out[rank] = (ms, bench.job_throughput(1e9, 5, ms, world))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo_world2():
+    torch = pytest.importorskip("torch")
+    mp = torch.multiprocessing.get_context("spawn")
+    mgr = mp.Manager()
+    out = mgr.dict()
+    times = [100.0, 125.0]
+    port = _free_port()
+    procs = [mp.Process(target=_rank_main, args=(r, 2, port, times, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    for r in range(2):
+        ms, value = out[r]
+        assert ms == 125.0  # every rank sees the slowest rank's time
+        assert math.isclose(value, 2 * 1e9 * 5 / 0.125 / 1e9)
+
+
+def test_reference_arm_other_ranks_do_nothing(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--gpus", "2"])
+    bench.run_reference(bench.parse())
+    assert capsys.readouterr().out == ""
