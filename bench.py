@@ -38,8 +38,8 @@ WORKLOAD = "gate sweep, 30-qubit complex128 state (16 GiB): Haar 1q on targets 0
 # DRAM bytes (read + write) per launch from one ncu capture at 26 qubits, scaled
 # to 30 qubits by the amplitude count (profiles/k_dense_df_26q_c128.md).  Valid
 # for the float-float kernels as profiled; other variants report null.
-NCU_TRAFFIC_30Q = {("k_dense1", "c128", "df"): (1.073761e9 + 1.012323e9) * 16,
-                   ("k_dense2", "c128", "df"): (1.073923e9 + 1.012535e9) * 16}
+NCU_TRAFFIC_30Q = {("k_dense1", "c128", "df"): (1.073801e9 + 1.012319e9) * 16,
+                   ("k_dense2", "c128", "df"): (1.073799e9 + 1.012004e9) * 16}
 
 
 def parse():
