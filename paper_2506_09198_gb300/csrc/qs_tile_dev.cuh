@@ -111,8 +111,19 @@ struct TileF32 {
   static __device__ __forceinline__ Sm to_sm(Glob g) { return g; }
   static __device__ __forceinline__ Glob from_sm(Sm s) { return s; }
   static __device__ __forceinline__ M::Val val(Sm s) { return M::load(s); }
+  // One 16-byte load per coefficient (a and b together).
+  static __device__ __forceinline__ float4 ldc4(const M::Coef* c) { return *reinterpret_cast<const float4*>(c); }
   template <int K>
-  static __device__ __forceinline__ Sm mac(const M::Coef* c, const M::Val* v) { return M::mac_round<K>(c, v); }
+  static __device__ __forceinline__ Sm mac(const M::Coef* c, const M::Val* v) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float4 q = ldc4(c + k);
+      acc = k == 0 ? mul2(make_float2(q.x, q.y), v[0].v) : fma2(make_float2(q.x, q.y), v[k].v, acc);
+      acc = fma2(make_float2(q.z, q.w), v[k].vs, acc);
+    }
+    return acc;
+  }
   // Real coefficients: the (-mi, mi) terms are zero and skipped.
   template <int K>
   static __device__ __forceinline__ Sm mac_real(const M::Coef* c, const M::Val* v) {
@@ -125,7 +136,7 @@ struct TileF32 {
   static __device__ __forceinline__ int mexp(const M::Val*) { return 0; }
   template <int K>
   static __device__ __forceinline__ Sm mac_rows(const M::Coef* c, const M::Val* v, int, int) {
-    return M::mac_round<K>(c, v);
+    return mac<K>(c, v);
   }
   static __device__ __forceinline__ Sm neg(Sm a) {
     return make_float2(__uint_as_float(__float_as_uint(a.x) ^ 0x80000000u),
