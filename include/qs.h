@@ -188,7 +188,12 @@ typedef struct {
  * keeps the block's amplitudes on chip for all of its gates (related work,
  * Sec. I: gate fusion and cache blocking).  Result equals applying the
  * gates one by one, up to rounding; permutations and SWAPs move amplitudes
- * exactly.  opts may be NULL (autotuned, no graph). */
+ * exactly.  Between consecutive complex128 fused blocks the device memory
+ * holds the state in an internal float-float form; it is back in (re, im)
+ * doubles when the call's work completes on the stream.  If the call fails
+ * after launching work (a device error or timeout at the next synchronous
+ * call), the state's contents are unspecified.  opts may be NULL
+ * (autotuned, no graph). */
 qs_status qs_fuse_run(qs_state s, const qs_circuit* c, const qs_run_opts* opts);
 
 /* Autotuner for fusion: run circuit c on s with every fusion setting
@@ -202,10 +207,13 @@ qs_status qs_fuse_run(qs_state s, const qs_circuit* c, const qs_run_opts* opts);
 qs_status qs_autotune(qs_state s, const qs_circuit* c, int* best_max_fuse, double* best_ms);
 
 /* Run circuits[i] on states[i] for i < count (distinct states, one dtype and
- * math mode), asynchronously on the first state's stream.  States of at most
- * 16 qubits run in one persistent launch: CTAs claim whole states, largest
- * estimated cost first, and apply each state's fused blocks in shared
- * memory.  Wider states follow as fused whole-GPU blocks.  opts->use_graph:
+ * math mode), asynchronously on the first state's stream.  Each state's
+ * circuit is compiled into fused blocks (as qs_fuse_run does).  States that
+ * fit one tile (11 qubits complex128, 12 complex64) run in one persistent
+ * launch: CTAs claim whole states, largest estimated cost first.  States of
+ * up to 16 qubits follow block by block: launch k applies block k of every
+ * such state, its tiles spread over the GPU.  Wider states follow as fused
+ * whole-GPU blocks (qs_fuse_run).  opts->use_graph:
  * capture the whole sequence as a CUDA graph, cached per (states, circuits)
  * pointer list and replayed by later calls with the same lists (the circuit
  * contents must not change in between).  Other states' streams are
