@@ -584,7 +584,7 @@ qs_status batch_run(qs_state* states, const qs_circuit* const* circuits, int cou
     if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
       return fail(QS_ERR_ARG, "a state appears twice in the batch");
   }
-  if (s0->dtype == QS_C64) return run_batch<TileF32>(states, circuits, count, opts);
+  if (s0->dtype == QS_C64) return run_batch<TileF32Batch>(states, circuits, count, opts);
   if (s0->math == QS_MATH_FP64) return run_batch<TileF64>(states, circuits, count, opts);
   return run_batch<TileDF>(states, circuits, count, opts);
 }

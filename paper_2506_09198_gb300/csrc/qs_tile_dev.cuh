@@ -101,6 +101,9 @@ __device__ __forceinline__ bool consumers_any(bool v) {
 // ---------------------------------------------------------------------------
 struct TileF32 {
   using M = MathF32;
+  // Uncontrolled 4x4 ops take the quads two at a time (one coefficient load
+  // serves both); the batched kernel, with more live state, opts out.
+  static constexpr bool kQuadPairs = true;
   // Stage the block's ops and coefficients in shared memory.
   static constexpr bool kStagePlan = true;
   using Glob = float2;
@@ -121,6 +124,17 @@ struct TileF32 {
       const float4 q = ldc4(c + k);
       acc = k == 0 ? mul2(make_float2(q.x, q.y), v[0].v) : fma2(make_float2(q.x, q.y), v[k].v, acc);
       acc = fma2(make_float2(q.z, q.w), v[k].vs, acc);
+    }
+    return acc;
+  }
+  // A row of four coefficients already in registers ((a, b) per float4).
+  static __device__ __forceinline__ Sm mac4(const float4* c, const M::Val* v) {
+    float2 acc = mul2(make_float2(c[0].x, c[0].y), v[0].v);
+    acc = fma2(make_float2(c[0].z, c[0].w), v[0].vs, acc);
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+      acc = fma2(make_float2(c[k].x, c[k].y), v[k].v, acc);
+      acc = fma2(make_float2(c[k].z, c[k].w), v[k].vs, acc);
     }
     return acc;
   }
@@ -156,12 +170,18 @@ struct TileF32 {
   }
 };
 
+// complex64 policy of the batched kernel: one quad at a time.
+struct TileF32Batch : TileF32 {
+  static constexpr bool kQuadPairs = false;
+};
+
 __device__ __forceinline__ double dneg(double x) {
   return __hiloint2double(__double2hiint(x) ^ (int)0x80000000u, __double2loint(x));
 }
 
 struct TileF64 {
   using M = MathF64;
+  static constexpr bool kQuadPairs = false;
   // Stage the block's ops and coefficients in shared memory.
   static constexpr bool kStagePlan = true;
   using Glob = double2;
@@ -205,6 +225,7 @@ struct TileF64 {
 // Float-float tile element: (re_h, im_h, re_l, im_l), |l| <= ulp(h)/2.
 struct TileDF {
   using M = MathDF;
+  static constexpr bool kQuadPairs = false;
   // The float-float plan stays in the parameter bank: staged in shared
   // memory, the compiler keeps more of it live and spills.
   static constexpr bool kStagePlan = false;
@@ -445,9 +466,51 @@ struct RegTile {
     }
   }
 
+  // The i-th register whose bits B0 and B1 are clear (a quad's base).
+  static constexpr int quad_base(int i, int b01) {
+    int c = 0;
+    for (int r = 0; r < R; ++r) {
+      if (r & b01) continue;
+      if (c == i) return r;
+      ++c;
+    }
+    return 0;
+  }
+
   template <int K0, int K1>
   __device__ __forceinline__ void dense2(const Coef* cf, uint32_t lmask, const uint8_t* rexp) {
     constexpr int B0 = 1 << K0, B1 = 1 << K1;
+    if constexpr (TP::kQuadPairs) {
+      if (lmask == 0) {
+        // complex64, no controls: two quads per pass over the matrix, so
+        // each row of coefficients is loaded once for both.
+#pragma unroll
+        for (int p = 0; p < R / 4; p += 2) {
+          constexpr int kB = B0 | B1;
+          const int ra = quad_base(p, kB), rb = quad_base(p + 1, kB);
+          const Val xa[4] = {TP::val(v[ra]), TP::val(v[ra | B0]), TP::val(v[ra | B1]), TP::val(v[ra | B0 | B1])};
+          const Val xb[4] = {TP::val(v[rb]), TP::val(v[rb | B0]), TP::val(v[rb | B1]), TP::val(v[rb | B0 | B1])};
+          Sm oa[4], ob[4];
+#pragma unroll
+          for (int row = 0; row < 4; ++row) {
+            float4 c[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) c[k] = TP::ldc4(cf + 4 * row + k);
+            oa[row] = TP::mac4(c, xa);
+            ob[row] = TP::mac4(c, xb);
+          }
+          v[ra] = oa[0];
+          v[ra | B0] = oa[1];
+          v[ra | B1] = oa[2];
+          v[ra | B0 | B1] = oa[3];
+          v[rb] = ob[0];
+          v[rb | B0] = ob[1];
+          v[rb | B1] = ob[2];
+          v[rb | B0 | B1] = ob[3];
+        }
+        return;
+      }
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (r & (B0 | B1)) continue;
