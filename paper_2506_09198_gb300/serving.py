@@ -56,7 +56,7 @@ class _Active:
     req: Request
     state: "qs.State"
     offset: int
-    chunks: List["qs.Circuit"]
+    n_chunks: int
     pos: int = 0
     stream: object = None
 
@@ -148,9 +148,15 @@ class Server:
             raise ValueError(f"request {req.rid}: {req.n} qubits exceed the HBM budget")
         heapq.heappush(self.pending, (req.arrival, req.rid, req))
 
-    def _chunks(self, gates) -> List["qs.Circuit"]:
-        return [qs.Circuit(gates[i:i + self.chunk_gates]) for i in range(0, len(gates), self.chunk_gates)] or \
-            [qs.Circuit([])]
+    def _n_chunks(self, gates) -> int:
+        return max(1, -(-len(gates) // self.chunk_gates))
+
+    def _chunk(self, a: "_Active") -> "qs.Circuit":
+        """The request's next chunk, marshalled when it is issued: the
+        host work of one tick overlaps the device work of the previous one
+        (the library copies what it needs before the call returns)."""
+        i = a.pos * self.chunk_gates
+        return qs.Circuit(a.req.gates[i:i + self.chunk_gates])
 
     def _admit(self, now: float):
         while self.pending and self.pending[0][0] <= now and len(self.active) < self.max_resident:
@@ -169,7 +175,7 @@ class Server:
             st = qs.State(req.n, self.dtype, handle=h)
             qs.qs_init_basis(st.h, 0)
             req.admitted = now
-            self.active[req.rid] = _Active(req, st, off, self._chunks(req.gates), 0, stream)
+            self.active[req.rid] = _Active(req, st, off, self._n_chunks(req.gates), 0, stream)
             self.used += fp
             self.peak_used = max(self.peak_used, self.used)
 
@@ -178,11 +184,11 @@ class Server:
         small = [a for a in self.active.values() if a.req.n <= self.small_n]
         large = [a for a in self.active.values() if a.req.n > self.small_n]
         if small:
-            qs.qs_batch_run([a.state.h for a in small], [a.chunks[a.pos] for a in small])
+            qs.qs_batch_run([a.state.h for a in small], [self._chunk(a) for a in small])
             for a in small:
                 a.pos += 1
         for a in large:
-            qs.qs_fuse_run(a.state.h, a.chunks[a.pos], qs.run_opts(max_fuse=self.max_fuse))
+            qs.qs_fuse_run(a.state.h, self._chunk(a), qs.run_opts(max_fuse=self.max_fuse))
             a.pos += 1
         self.ticks += 1
 
@@ -202,7 +208,7 @@ class Server:
         a.req.norm = float(vals[1 << k])
 
     def _complete(self, clock):
-        for rid in [r for r, a in self.active.items() if a.pos >= len(a.chunks)]:
+        for rid in [r for r, a in self.active.items() if a.pos >= a.n_chunks]:
             a = self.active.pop(rid)
             self._read_result(a)
             a.req.finished = clock()
