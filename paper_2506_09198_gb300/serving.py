@@ -130,7 +130,15 @@ class Server:
         self.small_stream = torch.cuda.Stream()
         self.streams = [torch.cuda.Stream() for _ in range(4)]
         self.result_stream = torch.cuda.Stream()
-        self.result_buf = torch.zeros((1 << self.result_qubits) + 1, dtype=torch.float64, device="cuda")
+        self.reaper = torch.cuda.Stream()  # never given work: closing a finished state waits on nothing
+        # Result slots: reads are issued on the result stream and collected
+        # when their event has completed, so the scheduler never waits on them.
+        self.n_slots = 64
+        width = (1 << self.result_qubits) + 1
+        self.result_dev = torch.zeros((self.n_slots, width), dtype=torch.float64, device="cuda")
+        self.result_host = torch.zeros((self.n_slots, width), dtype=torch.float64, pin_memory=True)
+        self.free_slots = list(range(self.n_slots))
+        self.reading: List = []          # (active, slot, event, k)
         self._next_stream = 0
         self.used = 0
         self.active: Dict[int, _Active] = {}
@@ -192,45 +200,71 @@ class Server:
             a.pos += 1
         self.ticks += 1
 
-    def _read_result(self, a: _Active):
+    def _start_read(self, a: _Active, slot: int):
         """Marginals of the lowest qubits and the norm, computed without
-        allocation on one result stream (so result reads never overlap)."""
+        allocation on one result stream (so result reads never overlap) and
+        copied to pinned host memory asynchronously."""
+        torch = self.torch
         k = min(self.result_qubits, a.req.n)
         rs = self.result_stream
         rs.wait_stream(a.stream)
         ptr = self.arena.base + a.offset
-        qs.qs_probs_noalloc(ptr, a.req.n, self.dtype, list(range(k)), self.result_buf.data_ptr(), rs.cuda_stream)
-        qs.qs_probs_noalloc(ptr, a.req.n, self.dtype, [], self.result_buf.data_ptr() + 8 * (1 << k), rs.cuda_stream)
-        with self.torch.cuda.stream(rs):
-            host = self.result_buf[: (1 << k) + 1].to("cpu", non_blocking=False)
-        vals = host.numpy()
-        a.req.probs = vals[: 1 << k].copy()
-        a.req.norm = float(vals[1 << k])
+        out = self.result_dev[slot].data_ptr()
+        qs.qs_probs_noalloc(ptr, a.req.n, self.dtype, list(range(k)), out, rs.cuda_stream)
+        qs.qs_probs_noalloc(ptr, a.req.n, self.dtype, [], out + 8 * (1 << k), rs.cuda_stream)
+        with torch.cuda.stream(rs):
+            self.result_host[slot, : (1 << k) + 1].copy_(self.result_dev[slot, : (1 << k) + 1], non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(rs)
+        self.reading.append((a, slot, ev, k))
+
+    def _collect(self, clock, wait: bool = False):
+        """Finish the reads whose results have reached the host (with wait,
+        at least one)."""
+        if wait and self.reading and not any(r[2].query() for r in self.reading):
+            self.reading[0][2].synchronize()
+        keep = []
+        for entry in self.reading:
+            a, slot, ev, k = entry
+            if not ev.query():
+                keep.append(entry)
+                continue
+            vals = self.result_host[slot, : (1 << k) + 1].numpy()
+            a.req.probs = vals[: 1 << k].copy()
+            a.req.norm = float(vals[1 << k])
+            a.req.finished = clock()
+            # the state's memory returns to the arena only after its reads
+            qs.qs_set_stream(a.state.h, self.reaper.cuda_stream)
+            a.state.close()
+            self.arena.release(a.offset, self.footprint(a.req.n))
+            self.used -= self.footprint(a.req.n)
+            self.free_slots.append(slot)
+            self.done.append(a.req)
+        self.reading = keep
 
     def _complete(self, clock):
         for rid in [r for r, a in self.active.items() if a.pos >= a.n_chunks]:
             a = self.active.pop(rid)
-            self._read_result(a)
-            a.req.finished = clock()
-            # the state's memory returns to the arena only after the reads
-            self.result_stream.synchronize()
-            a.state.close()
-            self.arena.release(a.offset, self.footprint(a.req.n))
-            self.used -= self.footprint(a.req.n)
-            self.done.append(a.req)
+            while not self.free_slots:
+                self._collect(clock, wait=True)
+            self._start_read(a, self.free_slots.pop())
+        self._collect(clock)
 
     def run(self, clock=None) -> List[Request]:
         """Serve every submitted request; arrivals are honoured against
         ``clock`` (seconds, default: wall time since this call)."""
         t0 = time.perf_counter()
         clock = clock or (lambda: time.perf_counter() - t0)
-        while self.pending or self.active:
+        while self.pending or self.active or self.reading:
             now = clock()
             self._admit(now)
             if not self.active:
-                wait = self.pending[0][0] - clock()  # idle until the next arrival
-                if wait > 0:
-                    time.sleep(min(wait, 0.01))
+                if self.reading:
+                    self._collect(clock, wait=not self.pending)
+                if self.pending:
+                    wait = self.pending[0][0] - clock()  # idle until the next arrival
+                    if wait > 0:
+                        time.sleep(min(wait, 0.001 if self.reading else 0.01))
                 continue
             self._tick()
             self._complete(clock)
