@@ -115,7 +115,7 @@ class BuddyArena(BuddyAllocator):
 
 class Server:
     def __init__(self, dtype: int = qs.QS_C128, hbm_budget_bytes: int = 64 << 30, max_resident: int = 256,
-                 small_n: int = 16, chunk_gates: int = 128, max_fuse: int = 0, result_qubits: int = 8):
+                 small_n: int = 16, chunk_gates: int = 256, max_fuse: int = 0, result_qubits: int = 8):
         import torch
 
         self.torch = torch
