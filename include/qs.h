@@ -71,6 +71,10 @@ enum {
 
 /* ---- state lifetime -------------------------------------------------- */
 
+/* The first qs_create or qs_wrap on a device also fills the library's phase
+ * tables there (static device arrays, 40 KiB, by a synchronous copy), so it
+ * must not run inside a stream capture. */
+
 /* Allocate a state of n qubits (1 <= n <= QS_MAX_QUBITS) with cudaMalloc on
  * the current device and set it to |0...0>.  The handle owns the memory and
  * uses the legacy default stream until qs_set_stream.  QS_ERR_OOM if the
