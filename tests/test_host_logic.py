@@ -140,3 +140,52 @@ def test_reference_arm_other_ranks_do_nothing(monkeypatch, capsys):
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--gpus", "2"])
     bench.run_reference(bench.parse())
     assert capsys.readouterr().out == ""
+
+
+# -- circuit generators: structure as the workload readings state it --------
+def test_rqc_structure():
+    n, layers = 9, 6
+    gates = W.rqc(n, layers, seed=3)
+    per_layer = [n + len(range(layer % 2, n - 1, 2)) for layer in range(layers)]
+    assert len(gates) == sum(per_layer)
+    pos, prev = 0, [None] * n
+    for layer in range(layers):
+        ones = gates[pos:pos + n]
+        assert [g.targets[0] for g in ones] == list(range(n))
+        for q, g in enumerate(ones):
+            assert g.name in ("sx", "sy", "sw") and g.name != prev[q]  # never the previous choice
+            prev[q] = g.name
+            U = np.asarray(g.data)
+            assert np.allclose(U @ U.conj().T, np.eye(2), atol=1e-15)
+        czs = gates[pos + n:pos + per_layer[layer]]
+        assert [g.targets for g in czs] == [(a, a + 1) for a in range(layer % 2, n - 1, 2)]
+        pos += per_layer[layer]
+
+
+def test_qft_structure():
+    n = 7
+    gates = W.qft(list(range(n)))
+    hs = [g for g in gates if g.name == "h"]
+    cps = [g for g in gates if g.name == "cp"]
+    swaps = [g for g in gates if g.name == "swap"]
+    assert len(hs) == n and len(cps) == n * (n - 1) // 2 and len(swaps) == n // 2
+    for g in cps:  # CP(pi / 2^(j-k)) controlled by k < j on target j
+        k, j = g.ctrls[0], g.targets[0]
+        assert k < j
+        assert np.isclose(np.angle(np.asarray(g.data)[1, 1]), math.pi / (1 << (j - k)))
+    assert [g.targets for g in swaps] == [(q, n - 1 - q) for q in range(n // 2)]
+
+
+def test_grover_and_shor_parameters():
+    for n in range(2, 21):
+        theta = math.asin(2.0 ** (-n / 2))
+        r = W.grover_iterations(n)
+        assert (2 * r + 1) * theta <= math.pi / 2 + theta and r == math.floor(math.pi / (4 * theta))
+    rng = W.rng_for(9)
+    for n in range(8, 21):
+        m, t, N, a = W.shor_params(n, rng)
+        assert m == max(4, min(8, n // 2)) and t == n - m
+        assert N % 2 == 1 and any(N % p == 0 for p in range(3, N)) and max(9, 1 << (m - 1)) <= N < (1 << m)
+        assert 1 < a < N and math.gcd(a, N) == 1
+        tab = W.mulmod_table(pow(a, 2, N), N, m)
+        assert sorted(tab.tolist()) == list(range(1 << m))  # a permutation
