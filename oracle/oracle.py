@@ -25,28 +25,54 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qsim_oracle.c")
 _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
+# Timing build of the same source with the gate loops split over OpenMP
+# threads; every index's update is independent, so its states are bit-identical.
+_LIB_OMP_PATH = os.path.join(_BUILD_DIR, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
+_threads = 1
+
+
+def _gcc(out, extra):
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", *extra, "-fPIC", "-shared", "-o", tmp, _SRC])
+    os.replace(tmp, out)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction) and return the .so path."""
+    """Compile the oracle with gcc (no FMA contraction): the single-thread
+    parity build and the OpenMP timing build.  Returns the parity build's path."""
     os.makedirs(_BUILD_DIR, exist_ok=True)
-    stale = (not os.path.exists(_LIB_PATH)) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
-    if force or stale:
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC]
-        )
-        os.replace(tmp, _LIB_PATH)
+    for path, extra in ((_LIB_PATH, []), (_LIB_OMP_PATH, ["-fopenmp"])):
+        stale = (not os.path.exists(path)) or os.path.getmtime(path) < os.path.getmtime(_SRC)
+        if force or stale:
+            _gcc(path, extra)
     return _LIB_PATH
 
 
-def _load():
-    global _lib
+def set_threads(count: int) -> int:
+    """Gate loops on ``count`` threads (the OpenMP build) or, with 1, the
+    single-thread parity build (the default).  Returns the threads in use."""
+    global _threads
+    count = max(1, int(count))
     with _lock:
-        if _lib is None:
-            lib = ctypes.CDLL(build())
+        _threads = count
+    if count == 1:
+        return 1
+    return int(_load().oracle_set_threads(count))
+
+
+def threads() -> int:
+    return _threads
+
+
+def _load():
+    with _lock:
+        omp = _threads > 1
+        lib = _libs.get(omp)
+        if lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_OMP_PATH if omp else _LIB_PATH)
             p_amp = ctypes.c_void_p
             p_i32 = ctypes.POINTER(ctypes.c_int)
             p_f64 = ctypes.POINTER(ctypes.c_double)
@@ -60,11 +86,15 @@ def _load():
             lib.oracle_norm2.argtypes = [p_amp, i32]
             lib.oracle_norm2.restype = ctypes.c_double
             lib.oracle_probs.argtypes = [p_amp, i32, p_i32, i32, p_f64]
+            lib.oracle_set_threads.argtypes = [i32]
+            lib.oracle_set_threads.restype = i32
             for f in (lib.oracle_apply_1q, lib.oracle_apply_kq, lib.oracle_apply_diag,
                       lib.oracle_apply_perm, lib.oracle_probs):
                 f.restype = None
-            _lib = lib
-    return _lib
+            _libs[omp] = lib
+            if omp:
+                lib.oracle_set_threads(_threads)
+        return lib
 
 
 def _nqubits(psi: np.ndarray) -> int:

@@ -17,14 +17,34 @@
  *     Sec. III-A).
  * Readings of points where the paper is silent are stated at each function.
  *
- * Every loop below visits all 2^n indices in increasing order and skips the
- * ones a gate does not start from; nothing is blocked, fused or reordered.
- * Arithmetic is plain double with no FMA contraction (built with
- * -ffp-contract=off).
+ * Every loop below visits all 2^n indices and skips the ones a gate does not
+ * start from; nothing is blocked, fused or reordered.  Arithmetic is plain
+ * double with no FMA contraction (built with -ffp-contract=off).
+ *
+ * Two builds of this one file: the parity build (single thread, the loops
+ * run in increasing index order) and a timing build with -fopenmp, where
+ * the gate loops are split over threads.  Each index's update reads and
+ * writes only its own pair / group, so both builds compute bit-identical
+ * states.  The reductions (norm, marginals) stay sequential in both.
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the gate loops in the timing build (no effect otherwise);
+ * returns the count in use (1 in the parity build). */
+int oracle_set_threads(int count) {
+#ifdef _OPENMP
+  if (count > 0) omp_set_num_threads(count);
+  return omp_get_max_threads();
+#else
+  (void)count;
+  return 1;
+#endif
+}
 
 typedef struct {
   double re, im;
@@ -84,6 +104,7 @@ void oracle_apply_1q(amp_t* psi, int n, uint64_t ctrl_mask, int t, const double*
   const uint64_t half = 1ull << t;
   const amp_t u00 = mat_at(U, 2, 0, 0), u01 = mat_at(U, 2, 0, 1);
   const amp_t u10 = mat_at(U, 2, 1, 0), u11 = mat_at(U, 2, 1, 1);
+#pragma omp parallel for schedule(static)
   for (uint64_t up = 0; up < dim; ++up) {
     if (bit_of(up, t)) continue;
     if (!controls_on(up, ctrl_mask)) continue;
@@ -106,12 +127,12 @@ void oracle_apply_1q(amp_t* psi, int n, uint64_t ctrl_mask, int t, const double*
  */
 void oracle_apply_kq(amp_t* psi, int n, uint64_t ctrl_mask, const int* targets, int k, const double* M) {
   const uint64_t dim = 1ull << n;
-  const int sub = 1 << k;
+  const int sub = 1 << k; /* k <= 8: at most 256 entries */
   uint64_t tmask = 0;
   for (int j = 0; j < k; ++j) tmask |= 1ull << targets[j];
-  amp_t* v = (amp_t*)malloc(sizeof(amp_t) * (size_t)sub);
-  if (!v) return;
+#pragma omp parallel for schedule(static)
   for (uint64_t i = 0; i < dim; ++i) {
+    amp_t v[256];
     if (i & tmask) continue;
     if (!controls_on(i, ctrl_mask)) continue;
     for (int s = 0; s < sub; ++s) v[s] = psi[with_sub(i, targets, k, (uint64_t)s)];
@@ -121,7 +142,6 @@ void oracle_apply_kq(amp_t* psi, int n, uint64_t ctrl_mask, const int* targets, 
       psi[with_sub(i, targets, k, (uint64_t)r)] = acc;
     }
   }
-  free(v);
 }
 
 /*
@@ -132,6 +152,7 @@ void oracle_apply_kq(amp_t* psi, int n, uint64_t ctrl_mask, const int* targets, 
  */
 void oracle_apply_diag(amp_t* psi, int n, uint64_t ctrl_mask, const int* targets, int k, const double* d) {
   const uint64_t dim = 1ull << n;
+#pragma omp parallel for schedule(static)
   for (uint64_t i = 0; i < dim; ++i) {
     if (!controls_on(i, ctrl_mask)) continue;
     const uint64_t s = sub_index(i, targets, k);
@@ -150,6 +171,7 @@ void oracle_apply_perm(amp_t* psi, int n, uint64_t ctrl_mask, const int* targets
   amp_t* src = (amp_t*)malloc(sizeof(amp_t) * (size_t)dim);
   if (!src) return;
   memcpy(src, psi, sizeof(amp_t) * (size_t)dim);
+#pragma omp parallel for schedule(static)
   for (uint64_t i = 0; i < dim; ++i) {
     if (!controls_on(i, ctrl_mask)) continue;
     const uint64_t s = sub_index(i, targets, k);

@@ -230,17 +230,35 @@ def pin_qft_basis(O, ns=range(1, 12), seed=300):
             assert _maxerr(back, O.basis_state(n, x)) < 1e-13
 
 
+def grover_closed_form(n, marked, r):
+    """State after r iterations of the Grover circuit from |0...0>.
+
+    With theta = asin(2^(-n/2)), each textbook iteration rotates by 2 theta in
+    the plane of |marked> and the uniform superposition of the other indices,
+    so G^r H^n |0> = sin((2r+1) theta) |marked> + cos((2r+1) theta) |rest>,
+    |rest> the normalised sum of the other 2^n - 1 basis states.  The circuit
+    realises the diffusion as H X MCZ X H = I - 2|s><s|, the negative of the
+    textbook 2|s><s| - I, so each iteration also contributes a factor -1."""
+    theta = math.asin(2.0 ** (-n / 2))
+    sign = -1.0 if r % 2 else 1.0
+    psi = np.full(1 << n, sign * math.cos((2 * r + 1) * theta) / math.sqrt((1 << n) - 1), dtype=np.complex128)
+    psi[marked] = sign * math.sin((2 * r + 1) * theta)
+    return psi
+
+
 def pin_grover(O, ns=range(2, 13), seed=400):
     rng = W.rng_for(seed)
     for n in ns:
         marked = int(rng.integers(1 << n))
         theta = math.asin(2.0 ** (-n / 2))
-        for r in sorted({0, 1, 2, W.grover_iterations(n)}):
+        for r in sorted({0, 1, 2, 3, W.grover_iterations(n)}):
             psi = O.run_circuit(O.basis_state(n), W.grover(n, marked, r))
             p = np.abs(psi) ** 2
             assert abs(p[marked] - math.sin((2 * r + 1) * theta) ** 2) < 1e-12, f"Grover n={n} r={r}"
             others = np.delete(psi, marked)
             assert _maxerr(others, np.full(others.size, others[0])) < 1e-12
+            # every amplitude, signs included
+            assert _maxerr(psi, grover_closed_form(n, marked, r)) < 1e-12, f"Grover state n={n} r={r}"
 
 
 def shor_counting_distribution(t, a, N):
@@ -314,6 +332,21 @@ def pin_moves_exact(O, n=9, seed=700):
     assert np.array_equal(got, psi0[src])
 
 
+def pin_threaded_build_identical(O, n=14, seed=900):
+    """The OpenMP timing build computes bit-identical states: every index's
+    update touches only its own pair or group."""
+    gates = random_mixed_circuit(n, 40, seed) + W.shor_like(n, seed=seed)[0]
+    psi0 = W.random_state(n, W.rng_for(seed))
+    a = O.run_circuit(psi0.copy(), gates)
+    prev = O.threads()
+    try:
+        O.set_threads(4)
+        b = O.run_circuit(psi0.copy(), gates)
+    finally:
+        O.set_threads(prev)
+    assert np.array_equal(a, b)
+
+
 def pin_probs(O, n=10, seed=800):
     psi = W.random_state(n, W.rng_for(seed))
     p_all = (np.abs(psi) ** 2).reshape((2,) * n)
@@ -346,4 +379,5 @@ ALL_PINS = [
     pin_norm_and_inverse,
     pin_moves_exact,
     pin_probs,
+    pin_threaded_build_identical,
 ]
