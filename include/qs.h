@@ -2,8 +2,9 @@
  * qs.h — C ABI of libqs, a GB300 (sm_103a) state-vector gate engine.
  *
  * The library applies quantum gates to a state of 2^n complex amplitudes
- * held in GPU memory (arXiv 2506.09198, Sec. I: "applying gate matrices to
- * the state vector" is the core operation of full state-vector simulation).
+ * held in GPU memory.  arXiv 2506.09198 (Sec. I) names this multiplication
+ * of gate matrices into the state vector as the central step of full
+ * state-vector simulation.
  *
  * Layout (Sec. II-A, Fig. 1): amplitudes are stored array-of-structures,
  * (re, im) side by side: complex64 = two floats (8 bytes), complex128 = two
@@ -24,8 +25,10 @@
  * value, qs_last_error() returns a message for the calling thread.  The
  * library never aborts and never throws across this boundary.  Gate calls
  * are asynchronous on the state's stream: an error raised on the device
- * (for example a bounded wait that ran out) is reported by the next
- * synchronous call (qs_sync, qs_norm, qs_probs, qs_copy_out, qs_gather).
+ * (for example a bounded wait that ran out) is recorded in that state's own
+ * device error word and reported by the state's next synchronous call
+ * (qs_sync, qs_norm, qs_probs, qs_copy_out, qs_gather); other states are not
+ * affected.  A batched launch records its errors in the first state's word.
  *
  * Threads: a qs_state handle is not thread-safe; distinct handles may be
  * used from distinct threads.
@@ -180,8 +183,10 @@ typedef struct {
                          block may span (the block's tile holds 2^max_fuse
                          strided chunks); 0 = the qs_autotune choice for this
                          dtype, math mode and qubit count (4 if untuned) */
-  int32_t use_graph;  /* 1: capture the launch sequence as a CUDA graph and
-                         replay it (the graph is cached per circuit pointer) */
+  int32_t use_graph;  /* qs_batch_run only (qs_fuse_run ignores it): 1
+                         captures the call's launches as one CUDA graph and
+                         launches that (fewer launch gaps); nothing is reused
+                         across calls: qs_batch_compile does that */
   int32_t reserved[6];
 } qs_run_opts;
 
@@ -211,18 +216,38 @@ qs_status qs_fuse_run(qs_state s, const qs_circuit* c, const qs_run_opts* opts);
 qs_status qs_autotune(qs_state s, const qs_circuit* c, int* best_max_fuse, double* best_ms);
 
 /* Run circuits[i] on states[i] for i < count (distinct states, one dtype and
- * math mode), asynchronously on the first state's stream.  Each state's
- * circuit is compiled into fused blocks (as qs_fuse_run does).  States that
- * fit one tile (11 qubits complex128, 12 complex64) run in one persistent
- * launch: CTAs claim whole states, largest estimated cost first.  States of
- * up to 16 qubits follow block by block: launch k applies block k of every
- * such state, its tiles spread over the GPU.  Wider states follow as fused
- * whole-GPU blocks (qs_fuse_run).  opts->use_graph:
- * capture the whole sequence as a CUDA graph, cached per (states, circuits)
- * pointer list and replayed by later calls with the same lists (the circuit
- * contents must not change in between).  Other states' streams are
- * synchronised before the launch. */
+ * math mode, one device), asynchronously on the first state's stream.  Each
+ * state's circuit is compiled into fused blocks (as qs_fuse_run does).
+ * States that fit one tile (11 qubits complex128, 12 complex64) run in one
+ * persistent launch: CTAs claim whole states, largest estimated cost first.
+ * States of up to 20 qubits follow block by block: launch k applies block k
+ * of every such state, its tiles spread over the GPU.  Wider states follow as
+ * fused whole-GPU blocks (qs_fuse_run).  The first state's stream first waits
+ * for the work already queued on every other member's stream, and every
+ * other member's stream then waits for the batch (events; the host does not
+ * block).  The circuits are read before the call returns. */
 qs_status qs_batch_run(qs_state* states, const qs_circuit* const* circuits, int count, const qs_run_opts* opts);
+
+/* A compiled batch: the work of qs_batch_run compiled and captured as a CUDA
+ * graph once, then launched any number of times (each launch applies the
+ * circuits again to the states' current contents).  The handle owns its
+ * device workspace (one cudaMalloc at compile time) and copies everything it
+ * needs from the circuits, so they may be freed after qs_batch_compile.
+ * Destroying a member state invalidates the handle: qs_batch_launch then
+ * returns QS_ERR_ARG.  Not thread-safe per handle. */
+typedef struct qs_batch_s* qs_batch;
+
+/* Compile and capture (synchronous host work; device copies are queued on the
+ * first state's stream).  count >= 1; the arguments are checked as in
+ * qs_batch_run.  Must not run inside a stream capture. */
+qs_status qs_batch_compile(qs_state* states, const qs_circuit* const* circuits, int count, qs_batch* out);
+
+/* Launch the captured graph on the first state's current stream, with the
+ * same stream ordering against the other members as qs_batch_run. */
+qs_status qs_batch_launch(qs_batch b);
+
+/* Wait for the handle's last launch, then release it.  NULL is accepted. */
+qs_status qs_batch_destroy(qs_batch b);
 
 /* ---- reductions (synchronous) ---------------------------------------- */
 
@@ -243,9 +268,12 @@ qs_status qs_probs(qs_state s, const int* qubits, int k, double* out);
  * hold only raw device pointers, call this instead.  It allocates nothing:
  * its scratch is a fixed array of 2^16 doubles (512 KiB) inside the library's
  * device image, held by every GPU that loads the library until exit.
- *   device_state  2^n amplitudes of dtype, device memory, 16-byte aligned
+ *   device_state  2^n amplitudes of dtype, device memory of the current GPU,
+ *                 16-byte aligned (host memory or another GPU's memory is
+ *                 rejected with QS_ERR_ARG)
  *   qubits, k     0 <= k <= min(16, n) distinct qubits (k = 0: out[0] = norm)
- *   device_out    2^k doubles of device memory (8-byte aligned), written
+ *   device_out    2^k doubles of device memory of the current GPU (8-byte
+ *                 aligned, checked like device_state), written
  *                 asynchronously on stream (NULL: legacy default stream)
  * Larger k is rejected with QS_ERR_ARG.  The first call on each device looks
  * up the scratch address on the current device; make it before any stream
@@ -254,6 +282,16 @@ qs_status qs_probs(qs_state s, const int* qubits, int k, double* out);
  * a call reads is written by that call first. */
 qs_status qs_probs_noalloc(const void* device_state, int n, qs_dtype dtype, const int* qubits, int k,
                            double* device_out, void* stream);
+
+/* Limit of every bounded wait inside the fused and batched kernels (a wait
+ * on a tile copy or on the warps that consume it), in seconds, 0 to 60;
+ * default 2.  Applies to launches queued after the call, process-wide.  A
+ * wait that runs out stops the kernel early: the kernel records
+ * QS_ERR_TIMEOUT in the state's error word, lets its own copies land and
+ * returns, so the context stays usable and the state's contents are
+ * unspecified.  Production code keeps the default; a short limit is for
+ * testing that path. */
+qs_status qs_set_wait_limit(double seconds);
 
 /* Wait for the state's stream with a host-side deadline: QS_ERR_TIMEOUT if
  * it has not drained after timeout_s seconds (the work is not cancelled).

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <chrono>
 #include <mutex>
 #include <new>
@@ -29,28 +30,65 @@ qs_status cuda_fail(cudaError_t e, const char* what) {
   return fail(st, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
 }
 
-// Device-side error word, one per device that loaded this module.
-__device__ uint32_t g_device_error;
+// Device-side error words, one per live state (per device that loaded this
+// module).  Slot 0 is shared by the states created once every other slot is
+// taken; a nonzero word means that a bounded wait of a kernel working on the
+// slot's state ran out.
+constexpr int kErrSlots = 8192;
+__device__ uint32_t g_err_words[kErrSlots];
 
-uint32_t* device_error_word(int device) {
+namespace {
+std::mutex g_slot_mu;
+std::vector<int> g_free_slots;
+bool g_slots_init = false;
+std::atomic<uint64_t> g_wait_ns{2000000000ull};
+
+int acquire_err_slot() {
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  if (!g_slots_init) {
+    for (int i = kErrSlots - 1; i >= 1; --i) g_free_slots.push_back(i);
+    g_slots_init = true;
+  }
+  if (g_free_slots.empty()) return 0;
+  const int slot = g_free_slots.back();
+  g_free_slots.pop_back();
+  return slot;
+}
+
+void release_err_slot(int slot) {
+  if (slot <= 0) return;
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  g_free_slots.push_back(slot);
+}
+
+uint32_t* err_words(int device) {
   static std::mutex mu;
   static void* addr[64] = {nullptr};
   std::lock_guard<std::mutex> lk(mu);
   if (device < 0 || device >= 64) return nullptr;
   if (!addr[device]) {
-    if (cudaGetSymbolAddress(&addr[device], g_device_error) != cudaSuccess) addr[device] = nullptr;
+    if (cudaGetSymbolAddress(&addr[device], g_err_words) != cudaSuccess) addr[device] = nullptr;
   }
   return (uint32_t*)addr[device];
 }
+}  // namespace
+
+uint32_t* error_word(qs_state s) {
+  uint32_t* base = err_words(s->device);
+  return base ? base + s->err_slot : nullptr;
+}
+
+uint64_t wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
 
 qs_status device_error_check(qs_state s) {
   uint32_t v = 0;
-  cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_device_error, sizeof(v), 0, cudaMemcpyDeviceToHost, s->stream);
+  const size_t off = (size_t)s->err_slot * sizeof(uint32_t);
+  cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_err_words, sizeof(v), off, cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "device error check");
   if (v != 0) {
     const uint32_t zero = 0;
-    cudaMemcpyToSymbolAsync(g_device_error, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, s->stream);
+    cudaMemcpyToSymbolAsync(g_err_words, &zero, sizeof(zero), off, cudaMemcpyHostToDevice, s->stream);
     cudaStreamSynchronize(s->stream);
     if (v == 1) return fail(QS_ERR_TIMEOUT, "a device-side bounded wait ran out (code %u)", v);
     return fail(QS_ERR_DEVICE, "device-side check failed (code %u)", v);
@@ -190,6 +228,7 @@ qs_status qs_create(int n, qs_dtype dtype, qs_state* out) {
     return cuda_fail(e, "cudaMalloc(state)");
   }
   s->owns = true;
+  s->err_slot = acquire_err_slot();
   st = ensure_phase_tables(s->device);
   if (st == QS_OK) st = launch_init_basis(s, 0);
   if (st == QS_OK) {
@@ -197,6 +236,7 @@ qs_status qs_create(int n, qs_dtype dtype, qs_state* out) {
     if (e != cudaSuccess) st = cuda_fail(e, "init");
   }
   if (st != QS_OK) {
+    release_err_slot(s->err_slot);
     cudaFree(s->psi);
     delete s;
     return st;
@@ -229,6 +269,7 @@ qs_status qs_wrap(int n, qs_dtype dtype, void* device_ptr, void* stream, qs_stat
     delete s;
     return st;
   }
+  s->err_slot = acquire_err_slot();
   *out = s;
   return QS_OK;
 }
@@ -237,6 +278,15 @@ qs_status qs_destroy(qs_state s) {
   if (!s) return QS_OK;
   cudaStreamSynchronize(s->stream);
   release_plan_cache(s);
+  if (s->err_slot > 0) {
+    // The next owner of the slot starts from a clear word.
+    uint32_t* w = error_word(s);
+    if (w) {
+      cudaMemsetAsync(w, 0, sizeof(uint32_t), s->stream);
+      cudaStreamSynchronize(s->stream);
+    }
+    release_err_slot(s->err_slot);
+  }
   if (s->owns && s->psi) cudaFree(s->psi);
   if (s->scratch) cudaFree(s->scratch);
   if (s->host_scratch) cudaFreeHost(s->host_scratch);
@@ -384,6 +434,12 @@ qs_status qs_probs(qs_state s, const int* qubits, int k, double* out) {
   uint64_t cm = 0;
   if ((st = check_qubits(s, nullptr, 0, qubits, k, &cm)) != QS_OK) return st;
   return run_probs(s, qubits, k, out);
+}
+
+qs_status qs_set_wait_limit(double seconds) {
+  if (!(seconds >= 0.0) || seconds > 60.0) return fail(QS_ERR_ARG, "wait limit %g s outside [0, 60]", seconds);
+  g_wait_ns.store((uint64_t)(seconds * 1e9), std::memory_order_relaxed);
+  return QS_OK;
 }
 
 qs_status qs_sync(qs_state s, double timeout_s) {

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <new>
 #include <numeric>
 #include <type_traits>
 #include <vector>
@@ -32,8 +33,10 @@ qs_status check_gate(const qs_state s, const qs_circuit* c, int64_t gi);  // qs_
 qs_status run_fused(qs_state s, const qs_circuit* c, int max_high);          // qs_tile.cu
 int fuse_width_for(qs_state s);                                              // qs_circuit.cu
 
-// Widest state that the persistent batched kernel runs on a single CTA.
-constexpr int kBatchLocalMax = 16;
+// Widest state that the batched launches take (single-tile states whole on
+// one CTA, wider ones block by block over the grid); wider states run as
+// fused whole-GPU blocks.
+constexpr int kBatchLocalMax = 20;
 
 struct BatchBlock {
   int L, m, nops, fmt;  // fmt: kTileInFF / kTileOutFF (float-float state between a state's blocks)
@@ -68,6 +71,7 @@ struct BatchArgs {
   uint32_t n_states;
   uint32_t* counter;  // next state to claim (zeroed before the launch)
   uint32_t* err;
+  uint64_t wait_ns;   // limit of each bounded wait
 };
 
 // Shared memory for staging one block's plan (as in k_tile: keeps two CTAs
@@ -116,7 +120,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_batch(const Batc
     // Make stage s free: store the tile it holds once the consumers are done.
     auto release = [&](int s) -> bool {
       if (!pending[s]) return true;
-      if (!mbar_wait(&done[s], (pend_j[s] / kStages) & 1u, a.err)) return false;
+      if (!mbar_wait(&done[s], (pend_j[s] / kStages) & 1u, a.err, a.wait_ns)) return false;
       const BatchBlock& b = a.blocks[pend_block[s]];
       const uint32_t chunk_bytes = (uint32_t)sizeof(Glob) << b.L;
       const uint64_t base = tile_base(pend_tau[s], b.L, b.m, b.base_high);
@@ -187,7 +191,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_batch(const Batc
       for (uint32_t jj = (j > (uint32_t)kStages ? j - kStages : 0u); jj < j; ++jj) {
         const int s = (int)(jj % kStages);
         const uint64_t t0 = global_ns();
-        while (!mbar_try(&full[s], (jj / kStages) & 1u) && global_ns() - t0 < kWaitNs) {
+        while (!mbar_try(&full[s], (jj / kStages) & 1u) && global_ns() - t0 < kDrainNs) {
         }
       }
       bulk_wait_all();
@@ -199,7 +203,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_batch(const Batc
   uint32_t staged = 0xFFFFFFFFu;
   for (uint32_t j = 0;; ++j) {
     const int s = (int)(j % kStages);
-    const bool ok = mbar_wait(&full[s], (j / kStages) & 1u, a.err);
+    const bool ok = mbar_wait(&full[s], (j / kStages) & 1u, a.err, a.wait_ns);
     if (consumers_any(!ok)) break;
     const TileDesc d = desc[s];
     if (d.block == 0xFFFFFFFFu) break;
@@ -241,9 +245,9 @@ namespace {
 
 using namespace fuser;
 
-struct BatchCache {
-  std::vector<const void*> key;  // states and circuit pointers of the cached batch
-  int dtype = -1, math = -1;
+// Device image of one compiled batch: work items, blocks, ops, coefficients,
+// permutation tables and the claim counters.
+struct BatchWork {
   void* dev = nullptr;
   size_t dev_bytes = 0;
   size_t off_states = 0, off_blocks = 0, off_ops = 0, off_coefs = 0, off_perm = 0, off_counter = 0;
@@ -252,20 +256,19 @@ struct BatchCache {
   // its tiles spread over the grid as separate work items (one launch each).
   std::vector<size_t> step_off;
   std::vector<uint32_t> step_n;
-  cudaGraphExec_t graph = nullptr;
-  int grid = 0;
-  size_t smem = 0;
 };
 
 std::mutex g_batch_mu;
-// One compiled-batch workspace per (device, stream): reuse is ordered by the
-// stream, so no launch can see a workspace that a later call overwrites.
-std::map<std::pair<int, cudaStream_t>, BatchCache*> g_batch_caches;
+// One-shot batches (qs_batch_run) compile into one workspace per (device,
+// stream): reuse is ordered by the stream, so no launch can see a workspace
+// that a later call overwrites.
+std::map<std::pair<int, cudaStream_t>, BatchWork*> g_oneshot_work;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 template <class TP>
-qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int count, BatchCache* bc) {
+qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int count, BatchWork* bw,
+                        cudaStream_t stream) {
   using Coef = typename TP::M::Coef;
   const int min_chunk = sizeof(typename TP::Glob) == 16 ? 3 : 4;
   const Limits lim{1 << 20, 65535, 65535};
@@ -387,52 +390,52 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
   }
 
   size_t off = 0;
-  bc->off_states = off;
+  bw->off_states = off;
   off = align_up(off + sorted.size() * sizeof(BatchState), 256);
   const size_t off_steps = off;
   off = align_up(off + step_items.size() * sizeof(BatchState), 256);
-  bc->off_blocks = off;
+  bw->off_blocks = off;
   off = align_up(off + blocks.size() * sizeof(BatchBlock), 256);
-  bc->off_ops = off;
+  bw->off_ops = off;
   off = align_up(off + ops.size() * sizeof(TileOp), 256);
-  bc->off_coefs = off;
+  bw->off_coefs = off;
   off = align_up(off + coefs.size() * sizeof(Coef), 256);
-  bc->off_perm = off;
+  bw->off_perm = off;
   off = align_up(off + perm.size() + 1, 256);
-  bc->off_counter = off;
+  bw->off_counter = off;
   off = align_up(off + (1 + (size_t)nsteps) * sizeof(uint32_t), 256);
-  if (bc->dev_bytes < off) {
-    if (bc->dev) {
-      cudaStreamSynchronize(states[0]->stream);
-      cudaFree(bc->dev);
-      bc->dev = nullptr;
-      bc->dev_bytes = 0;
+  if (bw->dev_bytes < off) {
+    if (bw->dev) {
+      cudaStreamSynchronize(stream);
+      cudaFree(bw->dev);
+      bw->dev = nullptr;
+      bw->dev_bytes = 0;
     }
-    QS_CUDA(cudaMalloc(&bc->dev, off));
-    bc->dev_bytes = off;
+    QS_CUDA(cudaMalloc(&bw->dev, off));
+    bw->dev_bytes = off;
   }
   std::vector<unsigned char> host(off, 0);
-  std::memcpy(host.data() + bc->off_states, sorted.data(), sorted.size() * sizeof(BatchState));
+  std::memcpy(host.data() + bw->off_states, sorted.data(), sorted.size() * sizeof(BatchState));
   if (!step_items.empty())
     std::memcpy(host.data() + off_steps, step_items.data(), step_items.size() * sizeof(BatchState));
-  std::memcpy(host.data() + bc->off_blocks, blocks.data(), blocks.size() * sizeof(BatchBlock));
-  std::memcpy(host.data() + bc->off_ops, ops.data(), ops.size() * sizeof(TileOp));
-  std::memcpy(host.data() + bc->off_coefs, coefs.data(), coefs.size() * sizeof(Coef));
-  if (!perm.empty()) std::memcpy(host.data() + bc->off_perm, perm.data(), perm.size());
+  std::memcpy(host.data() + bw->off_blocks, blocks.data(), blocks.size() * sizeof(BatchBlock));
+  std::memcpy(host.data() + bw->off_ops, ops.data(), ops.size() * sizeof(TileOp));
+  std::memcpy(host.data() + bw->off_coefs, coefs.data(), coefs.size() * sizeof(Coef));
+  if (!perm.empty()) std::memcpy(host.data() + bw->off_perm, perm.data(), perm.size());
   // Stream-ordered after the previous batch that used this buffer.
-  QS_CUDA(cudaMemcpyAsync(bc->dev, host.data(), off, cudaMemcpyHostToDevice, states[0]->stream));
-  bc->n_states = (uint32_t)sorted.size();
-  bc->step_off.resize(nsteps);
-  bc->step_n.resize(nsteps);
+  QS_CUDA(cudaMemcpyAsync(bw->dev, host.data(), off, cudaMemcpyHostToDevice, stream));
+  bw->n_states = (uint32_t)sorted.size();
+  bw->step_off.resize(nsteps);
+  bw->step_n.resize(nsteps);
   for (uint32_t k = 0; k < nsteps; ++k) {
-    bc->step_off[k] = off_steps + step_first[k] * sizeof(BatchState);
-    bc->step_n[k] = (uint32_t)step_count[k];
+    bw->step_off[k] = off_steps + step_first[k] * sizeof(BatchState);
+    bw->step_n[k] = (uint32_t)step_count[k];
   }
   return QS_OK;
 }
 
 template <class TP>
-qs_status launch_batch(qs_state s0, BatchCache* bc, cudaStream_t stream) {
+qs_status launch_batch(qs_state s0, const BatchWork* bw, cudaStream_t stream) {
   const size_t smem = kStages * ((size_t)sizeof(typename TP::Glob) << TP::kTileLog) + 2 * kStages * sizeof(uint64_t) +
                       kStages * sizeof(TileDesc) + (TP::kStagePlan ? kStageBytes : 0);
   auto kern = k_batch<TP>;
@@ -441,17 +444,18 @@ qs_status launch_batch(qs_state s0, BatchCache* bc, cudaStream_t stream) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTileThreads, smem) != cudaSuccess || occ < 1) occ = 1;
   const uint32_t full = (uint32_t)(sm_count(s0->device) * occ);
   BatchArgs<TP> args;
-  unsigned char* base = (unsigned char*)bc->dev;
-  args.blocks = (const BatchBlock*)(base + bc->off_blocks);
-  args.ops = (const TileOp*)(base + bc->off_ops);
-  args.coefs = (const typename TP::M::Coef*)(base + bc->off_coefs);
-  args.perm = base + bc->off_perm;
+  unsigned char* base = (unsigned char*)bw->dev;
+  args.blocks = (const BatchBlock*)(base + bw->off_blocks);
+  args.ops = (const TileOp*)(base + bw->off_ops);
+  args.coefs = (const typename TP::M::Coef*)(base + bw->off_coefs);
+  args.perm = base + bw->off_perm;
   args.phase_tab = static_cast<const typename TP::Phase*>(phase_table(s0->device, TP::kPhaseFormat));
   if (!args.phase_tab) return fail(QS_ERR_CUDA, "phase tables missing on device %d", s0->device);
-  uint32_t* counters = (uint32_t*)(base + bc->off_counter);
-  args.err = device_error_word(s0->device);
+  uint32_t* counters = (uint32_t*)(base + bw->off_counter);
+  args.err = error_word(s0);
   if (!args.err) return fail(QS_ERR_CUDA, "device error word unavailable");
-  QS_CUDA(cudaMemsetAsync(counters, 0, (1 + bc->step_n.size()) * sizeof(uint32_t), stream));
+  args.wait_ns = wait_limit_ns();
+  QS_CUDA(cudaMemsetAsync(counters, 0, (1 + bw->step_n.size()) * sizeof(uint32_t), stream));
   auto go = [&](const BatchState* items, uint32_t n, uint32_t* counter) -> qs_status {
     if (n == 0) return QS_OK;
     args.states = items;
@@ -461,87 +465,94 @@ qs_status launch_batch(qs_state s0, BatchCache* bc, cudaStream_t stream) {
     QS_CUDA(cudaGetLastError());
     return QS_OK;
   };
-  qs_status st = go((const BatchState*)(base + bc->off_states), bc->n_states, counters);
-  for (size_t k = 0; k < bc->step_n.size() && st == QS_OK; ++k)
-    st = go((const BatchState*)(base + bc->step_off[k]), bc->step_n[k], counters + 1 + k);
+  qs_status st = go((const BatchState*)(base + bw->off_states), bw->n_states, counters);
+  for (size_t k = 0; k < bw->step_n.size() && st == QS_OK; ++k)
+    st = go((const BatchState*)(base + bw->step_off[k]), bw->step_n[k], counters + 1 + k);
   return st;
 }
 
-template <class TP>
-qs_status run_batch(qs_state* states, const qs_circuit* const* circuits, int count, const qs_run_opts* opts) {
-  qs_state s0 = states[0];
-  if (!device_error_word(s0->device)) return fail(QS_ERR_CUDA, "device error word unavailable");
-  std::lock_guard<std::mutex> lk(g_batch_mu);
-  BatchCache*& slot = g_batch_caches[std::make_pair(s0->device, s0->stream)];
-  if (!slot) slot = new BatchCache();
-  BatchCache* bc = slot;
-  std::vector<const void*> key;
-  key.reserve(2 * (size_t)count);
-  for (int i = 0; i < count; ++i) {
-    key.push_back(states[i]);
-    key.push_back(circuits[i]);
-  }
-  const bool use_graph = opts && opts->use_graph;
-  const bool hit = use_graph && bc->graph && bc->key == key && bc->dtype == (int)s0->dtype && bc->math == (int)s0->math;
-  if (hit) {
-    QS_CUDA(cudaGraphLaunch(bc->graph, s0->stream));
-    return QS_OK;
-  }
-  if (bc->graph) {
-    cudaGraphExecDestroy(bc->graph);
-    bc->graph = nullptr;
-  }
-  // States up to kBatchLocalMax qubits share the persistent launch (one CTA
-  // each); wider states need the whole GPU per block and run as fused blocks
-  // after it, in the same stream order (and the same captured graph).
+// States up to kBatchLocalMax qubits share the batched launches; wider states
+// need the whole GPU per block and run as fused blocks after them, in the same
+// stream order.
+struct Split {
   std::vector<qs_state> local_states, wide_states;
   std::vector<const qs_circuit*> local_circuits, wide_circuits;
+};
+
+Split split_batch(qs_state* states, const qs_circuit* const* circuits, int count) {
+  Split sp;
   for (int i = 0; i < count; ++i) {
     if (states[i]->n <= kBatchLocalMax) {
-      local_states.push_back(states[i]);
-      local_circuits.push_back(circuits[i]);
+      sp.local_states.push_back(states[i]);
+      sp.local_circuits.push_back(circuits[i]);
     } else {
-      wide_states.push_back(states[i]);
-      wide_circuits.push_back(circuits[i]);
+      sp.wide_states.push_back(states[i]);
+      sp.wide_circuits.push_back(circuits[i]);
     }
   }
-  qs_status st = QS_OK;
-  if (!local_states.empty()) {
-    st = compile_batch<TP>(local_states.data(), local_circuits.data(), (int)local_states.size(), bc);
-    if (st != QS_OK) return st;
-  } else {
-    bc->n_states = 0;
-    bc->step_off.clear();
-    bc->step_n.clear();
+  return sp;
+}
+
+template <class TP>
+qs_status enqueue_batch(qs_state s0, const BatchWork* bw, const Split& sp, cudaStream_t stream) {
+  if (bw->n_states > 0 || !bw->step_n.empty()) {
+    qs_status r = launch_batch<TP>(s0, bw, stream);
+    if (r != QS_OK) return r;
   }
-  bc->key = key;
-  bc->dtype = (int)s0->dtype;
-  bc->math = (int)s0->math;
-  // Every state's pending work must finish before the batch touches it.
-  for (int i = 1; i < count; ++i)
-    if (states[i]->stream != s0->stream) QS_CUDA(cudaStreamSynchronize(states[i]->stream));
-  auto enqueue = [&](cudaStream_t stream) -> qs_status {
-    if (bc->n_states > 0 || !bc->step_n.empty()) {
-      qs_status r = launch_batch<TP>(s0, bc, stream);
-      if (r != QS_OK) return r;
-    }
-    for (size_t i = 0; i < wide_states.size(); ++i) {
-      qs_state w = wide_states[i];
-      cudaStream_t saved = w->stream;
-      w->stream = stream;
-      qs_status r = run_fused(w, wide_circuits[i], fuse_width_for(w));
-      w->stream = saved;
-      if (r != QS_OK) return r;
-    }
-    return QS_OK;
-  };
-  if (!use_graph) return enqueue(s0->stream);
+  for (size_t i = 0; i < sp.wide_states.size(); ++i) {
+    qs_state w = sp.wide_states[i];
+    cudaStream_t saved = w->stream;
+    w->stream = stream;
+    qs_status r = run_fused(w, sp.wide_circuits[i], fuse_width_for(w));
+    w->stream = saved;
+    if (r != QS_OK) return r;
+  }
+  return QS_OK;
+}
+
+// Make `stream` wait for the work queued so far on every member state's own
+// stream, without blocking the host.
+qs_status streams_join(qs_state* states, int count, cudaStream_t stream, cudaEvent_t ev) {
+  std::vector<cudaStream_t> seen;
+  for (int i = 0; i < count; ++i) {
+    cudaStream_t o = states[i]->stream;
+    if (o == stream || std::find(seen.begin(), seen.end(), o) != seen.end()) continue;
+    seen.push_back(o);
+    QS_CUDA(cudaEventRecord(ev, o));
+    QS_CUDA(cudaStreamWaitEvent(stream, ev, 0));
+  }
+  return QS_OK;
+}
+
+// Make every member state's own stream wait for the batch queued on `stream`.
+qs_status streams_fork(qs_state* states, int count, cudaStream_t stream, cudaEvent_t ev) {
+  QS_CUDA(cudaEventRecord(ev, stream));
+  std::vector<cudaStream_t> seen;
+  for (int i = 0; i < count; ++i) {
+    cudaStream_t o = states[i]->stream;
+    if (o == stream || std::find(seen.begin(), seen.end(), o) != seen.end()) continue;
+    seen.push_back(o);
+    QS_CUDA(cudaStreamWaitEvent(o, ev, 0));
+  }
+  return QS_OK;
+}
+
+cudaEvent_t order_event() {
+  static thread_local cudaEvent_t ev = nullptr;
+  if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) ev = nullptr;
+  return ev;
+}
+
+// Capture the batch's launches into an executable graph.
+template <class TP>
+qs_status capture_batch(qs_state s0, const BatchWork* bw, const Split& sp, cudaGraphExec_t* out) {
   cudaStream_t cap;
   QS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   cudaGraph_t g = nullptr;
+  qs_status st = QS_OK;
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    st = enqueue(cap);
+    st = enqueue_batch<TP>(s0, bw, sp, cap);
     e = cudaStreamEndCapture(cap, &g);
   }
   cudaStreamDestroy(cap);
@@ -550,18 +561,52 @@ qs_status run_batch(qs_state* states, const qs_circuit* const* circuits, int cou
     return st;
   }
   if (e != cudaSuccess) return cuda_fail(e, "batch graph capture");
-  e = cudaGraphInstantiate(&bc->graph, g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-  QS_CUDA(cudaGraphLaunch(bc->graph, s0->stream));
   return QS_OK;
+}
+
+template <class TP>
+qs_status run_batch(qs_state* states, const qs_circuit* const* circuits, int count, const qs_run_opts* opts) {
+  qs_state s0 = states[0];
+  if (!error_word(s0)) return fail(QS_ERR_CUDA, "device error word unavailable");
+  cudaEvent_t ev = order_event();
+  if (!ev) return fail(QS_ERR_CUDA, "event creation failed");
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  BatchWork*& slot = g_oneshot_work[std::make_pair(s0->device, s0->stream)];
+  if (!slot) slot = new BatchWork();
+  BatchWork* bw = slot;
+  const Split sp = split_batch(states, circuits, count);
+  if (!sp.local_states.empty()) {
+    qs_status st = compile_batch<TP>((qs_state*)sp.local_states.data(), sp.local_circuits.data(),
+                                     (int)sp.local_states.size(), bw, s0->stream);
+    if (st != QS_OK) return st;
+  } else {
+    bw->n_states = 0;
+    bw->step_off.clear();
+    bw->step_n.clear();
+  }
+  // Every state's pending work must finish before the batch touches it.
+  qs_status st = streams_join(states, count, s0->stream, ev);
+  if (st != QS_OK) return st;
+  if (opts && opts->use_graph) {
+    cudaGraphExec_t exec = nullptr;
+    st = capture_batch<TP>(s0, bw, sp, &exec);
+    if (st != QS_OK) return st;
+    cudaError_t e = cudaGraphLaunch(exec, s0->stream);
+    cudaGraphExecDestroy(exec);  // freed once the launch completes
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch(batch)");
+  } else {
+    st = enqueue_batch<TP>(s0, bw, sp, s0->stream);
+    if (st != QS_OK) return st;
+  }
+  return streams_fork(states, count, s0->stream, ev);
 }
 
 }  // namespace
 
-void release_batch_cache(qs_state s) { (void)s; }
-
-qs_status batch_run(qs_state* states, const qs_circuit* const* circuits, int count, const qs_run_opts* opts) {
+qs_status batch_check(qs_state* states, const qs_circuit* const* circuits, int count) {
   if (count < 0 || (count > 0 && (!states || !circuits))) return fail(QS_ERR_ARG, "bad batch");
   if (count == 0) return QS_OK;
   const qs_state s0 = states[0];
@@ -577,16 +622,138 @@ qs_status batch_run(qs_state* states, const qs_circuit* const* circuits, int cou
       if (st != QS_OK) return st;
     }
   }
-  {
-    std::vector<const void*> seen;
-    for (int i = 0; i < count; ++i) seen.push_back(states[i]->psi);
-    std::sort(seen.begin(), seen.end());
-    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
-      return fail(QS_ERR_ARG, "a state appears twice in the batch");
-  }
+  std::vector<const void*> seen;
+  for (int i = 0; i < count; ++i) seen.push_back(states[i]->psi);
+  std::sort(seen.begin(), seen.end());
+  if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+    return fail(QS_ERR_ARG, "a state appears twice in the batch");
+  return QS_OK;
+}
+
+qs_status batch_run(qs_state* states, const qs_circuit* const* circuits, int count, const qs_run_opts* opts) {
+  qs_status st = batch_check(states, circuits, count);
+  if (st != QS_OK || count == 0) return st;
+  const qs_state s0 = states[0];
   if (s0->dtype == QS_C64) return run_batch<TileF32Batch>(states, circuits, count, opts);
   if (s0->math == QS_MATH_FP64) return run_batch<TileF64>(states, circuits, count, opts);
   return run_batch<TileDF>(states, circuits, count, opts);
 }
 
 }  // namespace qs
+
+// ---------------------------------------------------------------------------
+// Compiled batches: compiled and captured once, launched many times
+// ---------------------------------------------------------------------------
+struct qs_batch_s {
+  qs::BatchWork work;  // owned device image
+  cudaGraphExec_t graph = nullptr;
+  cudaEvent_t last = nullptr;  // recorded after each launch
+  std::vector<qs_state> states;
+  bool valid = true;   // false once a member state has been destroyed
+};
+
+namespace qs {
+namespace {
+std::mutex g_live_mu;
+std::vector<qs_batch_s*> g_live_batches;
+}  // namespace
+
+// A destroyed state invalidates every compiled batch that holds it.
+void release_batch_cache(qs_state s) {
+  std::lock_guard<std::mutex> lk(g_live_mu);
+  for (qs_batch_s* b : g_live_batches)
+    if (b->valid && std::find(b->states.begin(), b->states.end(), s) != b->states.end()) b->valid = false;
+}
+
+template <class TP>
+qs_status compile_handle(qs_batch_s* b, qs_state* states, const qs_circuit* const* circuits, int count) {
+  qs_state s0 = states[0];
+  const Split sp = split_batch(states, circuits, count);
+  if (!sp.local_states.empty()) {
+    qs_status st = compile_batch<TP>((qs_state*)sp.local_states.data(), sp.local_circuits.data(),
+                                     (int)sp.local_states.size(), &b->work, s0->stream);
+    if (st != QS_OK) return st;
+  }
+  return capture_batch<TP>(s0, &b->work, sp, &b->graph);
+}
+
+}  // namespace qs
+
+using namespace qs;
+
+extern "C" {
+
+qs_status qs_batch_run(qs_state* states, const qs_circuit* const* circuits, int count, const qs_run_opts* opts) {
+  return batch_run(states, circuits, count, opts);
+}
+
+qs_status qs_batch_compile(qs_state* states, const qs_circuit* const* circuits, int count, qs_batch* out) {
+  if (!out) return fail(QS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (count < 1) return fail(QS_ERR_ARG, "a compiled batch needs at least one state");
+  qs_status st = batch_check(states, circuits, count);
+  if (st != QS_OK) return st;
+  qs_batch_s* b = new (std::nothrow) qs_batch_s();
+  if (!b) return fail(QS_ERR_OOM, "host allocation failed");
+  b->states.assign(states, states + count);
+  const qs_state s0 = states[0];
+  if (cudaEventCreateWithFlags(&b->last, cudaEventDisableTiming) != cudaSuccess) {
+    delete b;
+    return fail(QS_ERR_CUDA, "event creation failed");
+  }
+  if (s0->dtype == QS_C64)
+    st = compile_handle<TileF32Batch>(b, states, circuits, count);
+  else if (s0->math == QS_MATH_FP64)
+    st = compile_handle<TileF64>(b, states, circuits, count);
+  else
+    st = compile_handle<TileDF>(b, states, circuits, count);
+  if (st == QS_OK) {
+    // The workspace copy is queued on the first state's stream; the graph
+    // is launched there too, so it is ordered after the copy.
+    std::lock_guard<std::mutex> lk(g_live_mu);
+    g_live_batches.push_back(b);
+    *out = b;
+    return QS_OK;
+  }
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->work.dev) {
+    cudaStreamSynchronize(s0->stream);
+    cudaFree(b->work.dev);
+  }
+  cudaEventDestroy(b->last);
+  delete b;
+  return st;
+}
+
+qs_status qs_batch_launch(qs_batch b) {
+  if (!b) return fail(QS_ERR_ARG, "batch handle is NULL");
+  {
+    std::lock_guard<std::mutex> lk(g_live_mu);
+    if (!b->valid) return fail(QS_ERR_ARG, "a state of this compiled batch has been destroyed");
+  }
+  cudaEvent_t ev = order_event();
+  if (!ev) return fail(QS_ERR_CUDA, "event creation failed");
+  qs_state s0 = b->states[0];
+  qs_status st = streams_join(b->states.data(), (int)b->states.size(), s0->stream, ev);
+  if (st != QS_OK) return st;
+  QS_CUDA(cudaGraphLaunch(b->graph, s0->stream));
+  QS_CUDA(cudaEventRecord(b->last, s0->stream));
+  return streams_fork(b->states.data(), (int)b->states.size(), s0->stream, ev);
+}
+
+qs_status qs_batch_destroy(qs_batch b) {
+  if (!b) return QS_OK;
+  {
+    std::lock_guard<std::mutex> lk(g_live_mu);
+    g_live_batches.erase(std::remove(g_live_batches.begin(), g_live_batches.end(), b), g_live_batches.end());
+  }
+  // Launches in flight keep reading the workspace: wait for the last one.
+  cudaEventSynchronize(b->last);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->work.dev) cudaFree(b->work.dev);
+  cudaEventDestroy(b->last);
+  delete b;
+  return QS_OK;
+}
+
+}  // extern "C"

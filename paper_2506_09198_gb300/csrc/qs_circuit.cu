@@ -10,8 +10,6 @@
 namespace qs {
 
 qs_status run_fused(qs_state s, const qs_circuit* c, int max_high);  // qs_tile.cu
-qs_status batch_run(qs_state* states, const qs_circuit* const* circuits, int count,
-                    const qs_run_opts* opts);  // qs_batch.cu
 void release_batch_cache(qs_state s);           // qs_batch.cu
 
 void release_plan_cache(qs_state s) { release_batch_cache(s); }
@@ -184,10 +182,6 @@ qs_status qs_autotune(qs_state s, const qs_circuit* c, int* best_max_fuse, doubl
   if (best_max_fuse) *best_max_fuse = best;
   if (best_ms) *best_ms = best_t;
   return device_error_check(s);
-}
-
-qs_status qs_batch_run(qs_state* states, const qs_circuit* const* circuits, int count, const qs_run_opts* opts) {
-  return batch_run(states, circuits, count, opts);
 }
 
 }  // extern "C"

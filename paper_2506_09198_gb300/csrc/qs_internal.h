@@ -20,8 +20,9 @@ struct qs_state_s {
   size_t scratch_bytes = 0;
   void* host_scratch = nullptr;  // pinned host mirror for small results
   size_t host_scratch_bytes = 0;
-  // Fused-circuit cache (graph / plan), owned by qs_circuit.cu.
-  void* plan_cache = nullptr;
+  // Slot of this state's device-side error word (0: the shared overflow
+  // slot, used once every other slot is taken).
+  int err_slot = 0;
 };
 
 namespace qs {
@@ -36,11 +37,13 @@ qs_status cuda_fail(cudaError_t e, const char* what);
 
 inline size_t amp_bytes(qs_dtype dt) { return dt == QS_C64 ? 8 : 16; }
 
-// Device-side error word: kernels that run bounded waits or range checks
-// record a nonzero code here; qs_sync and every synchronous call read and
-// clear it.
+// Device-side error words: kernels that run bounded waits record a nonzero
+// code in the word of the state they work on; qs_sync and every synchronous
+// call on that state read and clear it.
 qs_status device_error_check(qs_state s);
-uint32_t* device_error_word(int device);
+uint32_t* error_word(qs_state s);
+// Limit of every bounded device-side wait, in nanoseconds (qs_set_wait_limit).
+uint64_t wait_limit_ns();
 
 // Number of resident CTAs per SM for a kernel, cached per function pointer.
 int sm_count(int device);

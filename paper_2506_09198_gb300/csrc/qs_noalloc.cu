@@ -82,6 +82,20 @@ extern "C" qs_status qs_probs_noalloc(const void* device_state, int n, qs_dtype 
   if (((uintptr_t)device_out) % 8 != 0) return fail(QS_ERR_ARG, "device_out must be 8-byte aligned");
   int device = 0;
   QS_CUDA(cudaGetDevice(&device));
+  // Both buffers must be device memory of the current GPU: a host pointer or
+  // another GPU's memory is an argument error, not a kernel fault.  (Looking
+  // up pointer attributes allocates nothing.)
+  const void* ptrs[2] = {device_state, device_out};
+  const char* names[2] = {"device_state", "device_out"};
+  for (int j = 0; j < 2; ++j) {
+    cudaPointerAttributes attr;
+    const cudaError_t e = cudaPointerGetAttributes(&attr, ptrs[j]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaPointerGetAttributes");
+    if (attr.type != cudaMemoryTypeDevice)
+      return fail(QS_ERR_ARG, "%s is not device memory (memory type %d)", names[j], (int)attr.type);
+    if (attr.device != device)
+      return fail(QS_ERR_ARG, "%s is on device %d, but device %d is current", names[j], attr.device, device);
+  }
   double* scratch = nullptr;
   qs_status st = scratch_for_device(device, &scratch);
   if (st != QS_OK) return st;

@@ -15,9 +15,10 @@
 // FP32 pipes without re-splitting doubles; they are rounded back to IEEE
 // double once before the store.
 //
-// Every wait is bounded (about 2 s of %globaltimer): on expiry the kernel
-// records QS_ERR_TIMEOUT's code in the device error word, all warps agree to
-// stop, the producer waits for the copies it issued, and the kernel returns.
+// Every wait is bounded (qs_set_wait_limit, 2 s of %globaltimer by default):
+// on expiry the kernel records QS_ERR_TIMEOUT's code in the state's device
+// error word, all warps agree to stop, the producer waits for the copies it
+// issued, and the kernel returns.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_tile(typename TP
       unsigned char* buf = smem + (size_t)s * tile_bytes;
       if (j >= (uint32_t)kStages) {
         const uint32_t jp = j - kStages;
-        if (!mbar_wait(&done[s], (jp / kStages) & 1u, err)) {
+        if (!mbar_wait(&done[s], (jp / kStages) & 1u, err, plan.wait_ns)) {
           ok = false;
           break;
         }
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_tile(typename TP
       const uint32_t first = count > (uint32_t)kStages ? count - kStages : 0u;
       for (uint32_t jj = first; jj < count; ++jj) {
         const int s = (int)(jj % kStages);
-        if (!mbar_wait(&done[s], (jj / kStages) & 1u, err)) {
+        if (!mbar_wait(&done[s], (jj / kStages) & 1u, err, plan.wait_ns)) {
           ok = false;
           break;
         }
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_tile(typename TP
       for (uint32_t jj = first; jj < loads_issued; ++jj) {
         const int s = (int)(jj % kStages);
         const uint64_t t0 = global_ns();
-        while (!mbar_try(&full[s], (jj / kStages) & 1u) && global_ns() - t0 < kWaitNs) {
+        while (!mbar_try(&full[s], (jj / kStages) & 1u) && global_ns() - t0 < kDrainNs) {
         }
       }
     }
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_tile(typename TP
     const uint64_t tau = blockIdx.x + (uint64_t)j * gridDim.x;
     if (tau >= plan.n_tiles) break;
     const int s = (int)(j % kStages);
-    const bool ok = mbar_wait(&full[s], (j / kStages) & 1u, err);
+    const bool ok = mbar_wait(&full[s], (j / kStages) & 1u, err, plan.wait_ns);
     if (consumers_any(!ok)) break;
     Sm* t = reinterpret_cast<Sm*>(smem + (size_t)s * tile_bytes);
     const uint64_t base = tile_base(tau, plan.L, plan.m, plan.base_high);
@@ -230,7 +231,7 @@ qs_status launch_plan(qs_state s, const TilePlan<typename TP::M::Coef>& plan) {
   }
   const uint64_t full = (uint64_t)sm_count(s->device) * occ;
   const unsigned grid = (unsigned)(plan.n_tiles < full ? plan.n_tiles : full);
-  uint32_t* err = device_error_word(s->device);
+  uint32_t* err = error_word(s);
   if (!err) return fail(QS_ERR_CUDA, "device error word unavailable");
   kern<<<grid, kTileThreads, smem, s->stream>>>((typename TP::Glob*)s->psi, plan, err);
   cudaError_t e = cudaGetLastError();
@@ -268,6 +269,7 @@ qs_status launch_block(qs_state s, const std::vector<FGate>& gates, const std::v
   TilePlan<Coef>* plan = reinterpret_cast<TilePlan<Coef>*>(plan_mem.data());
   fill_plan(plan, s->n, bo);
   plan->phase_tab = ptab;
+  plan->wait_ns = wait_limit_ns();
   return launch_plan<TP>(s, *plan);
 }
 
@@ -353,6 +355,7 @@ qs_status run_blocks(qs_state s, const std::vector<FGate>& gates, int max_high) 
     }
     fill_plan(plan, n, bo);
     plan->phase_tab = ptab;
+    plan->wait_ns = wait_limit_ns();
     const bool chained = kChain && pend_valid;
     qs_status st = flush(kChain);
     if (st != QS_OK) return st;

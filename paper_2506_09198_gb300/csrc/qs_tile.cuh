@@ -98,6 +98,7 @@ struct TilePlan {
   Coef coefs[kTileMaxCoefs];
   uint8_t perm[kTileMaxPermBytes];
   const void* phase_tab;               // exp(2 pi i v 2^(8b) / 2^32) at [256 b + v], the policy's format
+  uint64_t wait_ns;                    // limit of each bounded wait
 };
 
 // Tile storage in HBM between consecutive float-float blocks: the plan's

@@ -22,7 +22,9 @@ constexpr int kTileConsumers = 256;
 constexpr int kTileThreads = kTileConsumers + 32;
 constexpr int kStages = QS_TILE_STAGES;
 constexpr int kTileMinCtas = QS_TILE_MIN_CTAS;
-constexpr uint64_t kWaitNs = 2000000000ull;
+// Bound of the waits that let a CTA's own copies land before it exits after
+// an error (the copies are in-range and always complete).
+constexpr uint64_t kDrainNs = 2000000000ull;
 
 // ---------------------------------------------------------------------------
 // PTX helpers: mbarrier, bulk copies, proxy fence, named barriers
@@ -53,14 +55,14 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Bounded wait: false when it gave up (timeout recorded, or another thread
-// already recorded an error).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* err) {
+// Bounded wait (limit_ns of %globaltimer): false when it gave up (timeout
+// recorded, or another thread already recorded an error).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* err, uint64_t limit_ns) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (!mbar_try(bar, parity)) {
     if (*(volatile uint32_t*)err != 0u) return false;
-    if (global_ns() - t0 > kWaitNs) {
+    if (global_ns() - t0 > limit_ns) {
       atomicCAS(err, 0u, 1u);
       return false;
     }

@@ -82,6 +82,10 @@ _SIGS = {
     "qs_sync": [_P, ctypes.c_double],
     "qs_probs_noalloc": [_P, _I, _I, _PI, _I, _P, _P],
     "qs_autotune": [_P, ctypes.POINTER(qs_circuit), _PI, _PD],
+    "qs_batch_compile": [ctypes.POINTER(_P), ctypes.POINTER(ctypes.POINTER(qs_circuit)), _I, ctypes.POINTER(_P)],
+    "qs_batch_launch": [_P],
+    "qs_batch_destroy": [_P],
+    "qs_set_wait_limit": [ctypes.c_double],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -304,11 +308,36 @@ def qs_autotune(h, circuit: Circuit):
     return best.value, ms.value
 
 
-def qs_batch_run(handles, circuits, opts: qs_run_opts | None = None):
+def _batch_arrays(handles, circuits):
     n = len(handles)
     hs = (_P * n)(*[h.value if isinstance(h, _P) else h for h in handles])
     cs = (ctypes.POINTER(qs_circuit) * n)(*[c.ptr for c in circuits])
+    return n, hs, cs
+
+
+def qs_batch_run(handles, circuits, opts: qs_run_opts | None = None):
+    n, hs, cs = _batch_arrays(handles, circuits)
     _check(_lib.qs_batch_run(hs, cs, n, ctypes.byref(opts) if opts is not None else None))
+
+
+def qs_batch_compile(handles, circuits):
+    """Compile and capture a batch once; returns a handle for qs_batch_launch."""
+    n, hs, cs = _batch_arrays(handles, circuits)
+    b = _P()
+    _check(_lib.qs_batch_compile(hs, cs, n, ctypes.byref(b)))
+    return b
+
+
+def qs_batch_launch(b):
+    _check(_lib.qs_batch_launch(b))
+
+
+def qs_batch_destroy(b):
+    _check(_lib.qs_batch_destroy(b))
+
+
+def qs_set_wait_limit(seconds: float):
+    _check(_lib.qs_set_wait_limit(float(seconds)))
 
 
 # ---------------------------------------------------------------------------

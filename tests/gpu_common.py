@@ -2,6 +2,9 @@
 against the oracle on the same seeded inputs)."""
 from __future__ import annotations
 
+import contextlib
+import os
+
 import numpy as np
 
 # Accuracy bars: complex128 max amplitude error 1e-12 against the FP64
@@ -55,3 +58,30 @@ def assert_close(got, ref, mode, what=""):
             f = fidelity(got, ref)
             assert f >= C64_FID, f"{what}: fidelity {f:.9f} < {C64_FID}"
     return err
+
+
+def assert_state(got, ref, mode, what=""):
+    """The accuracy bar for long circuits: complex128 max amplitude error
+    1e-12; complex64 fidelity 1 - 1e-5 (its norm may drift by FP32 rounding
+    of the gate entries, which the fidelity does not count)."""
+    got = np.asarray(got, dtype=np.complex128)
+    ref = np.asarray(ref, dtype=np.complex128)
+    if mode.startswith("c128"):
+        err = float(np.max(np.abs(got - ref))) if got.size else 0.0
+        assert err <= C128_TOL, f"{what}: max abs error {err:.3e} > {C128_TOL}"
+        return err
+    f = fidelity(got, ref)
+    assert f >= C64_FID, f"{what}: fidelity {f:.9f} < {C64_FID}"
+    return 1.0 - f
+
+
+@contextlib.contextmanager
+def oracle_threads(O):
+    """Run the oracle's gate loops on every host core (the OpenMP build of
+    the same source: bit-identical states) for the large parity cases."""
+    prev = O.threads()
+    O.set_threads(os.cpu_count() or 1)
+    try:
+        yield
+    finally:
+        O.set_threads(prev)

@@ -55,7 +55,30 @@ def test_argument_validation_without_gpu(qs):
     assert lib.qs_destroy(None) == qs.QS_OK
     assert lib.qs_wrap(10, qs.QS_C128, None, None, ctypes.byref(h)) == qs.QS_ERR_ARG
     assert lib.qs_batch_run(None, None, -1, None) == qs.QS_ERR_ARG
+    b = ctypes.c_void_p()
+    assert lib.qs_batch_compile(None, None, 0, ctypes.byref(b)) == qs.QS_ERR_ARG
+    assert lib.qs_batch_compile(None, None, 1, None) == qs.QS_ERR_ARG
+    assert lib.qs_batch_launch(None) == qs.QS_ERR_ARG
+    assert lib.qs_batch_destroy(None) == qs.QS_OK
+    for bad in (-1.0, 61.0, float("nan")):
+        assert lib.qs_set_wait_limit(bad) == qs.QS_ERR_ARG
+    assert lib.qs_set_wait_limit(2.0) == qs.QS_OK
     assert qs.qs_version().startswith("libqs")
+
+
+def test_noalloc_rejects_host_memory_without_gpu(qs):
+    """A host buffer is never handed to a kernel: without a GPU the call fails
+    at the device lookup, with a GPU at the pointer check (QS_ERR_ARG)."""
+    import numpy as np
+
+    lib = qs.lib()
+    host = np.zeros(1 << 10, dtype=np.complex128)
+    out = np.zeros(4, dtype=np.float64)
+    q = (ctypes.c_int * 2)(0, 1)
+    st = lib.qs_probs_noalloc(ctypes.c_void_p(host.ctypes.data), 10, qs.QS_C128, q, 2,
+                              ctypes.c_void_p(out.ctypes.data), None)
+    assert st != qs.QS_OK
+    assert np.all(out == 0.0)
 
 
 def test_binding_raises_qserror(qs):

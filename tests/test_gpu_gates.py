@@ -201,19 +201,22 @@ def test_init_copy_gather(mode):
     st.close()
 
 
+@pytest.mark.parametrize("max_fuse", [1, 0, 6])
 @pytest.mark.parametrize("mode", MODES)
-def test_random_circuit_400_gates_n20(mode):
+def test_random_circuit_400_gates_n20(mode, max_fuse):
     """20-qubit state from |0...0>, 400 gates: Haar 2x2 on uniform targets,
-    CNOT on random distinct pairs at 30% of gates; full-state check."""
+    CNOT on random distinct pairs at 30% of gates; full-state check, gate by
+    gate (max_fuse 1) and through the fuser (0: the default width; 6: the
+    widest blocks)."""
     n = 20
     gates = W.random_circuit(n, 400, 0.3, seed=2506)
     psi0 = O.basis_state(n)
     ref = O.run_circuit(psi0.copy(), gates)
     st = new_state(n, mode)
-    st.run(gates, max_fuse=1)
+    st.run(gates, max_fuse=max_fuse)
     got = st.read()
     st.close()
-    assert_close(got, ref, mode, "random circuit n=20")
+    assert_close(got, ref, mode, f"random circuit n=20, max_fuse={max_fuse}")
 
 
 def test_errors_on_gpu():
