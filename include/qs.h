@@ -205,6 +205,16 @@ typedef struct {
  * (autotuned, no graph). */
 qs_status qs_fuse_run(qs_state s, const qs_circuit* c, const qs_run_opts* opts);
 
+/* Launch counts of the last qs_fuse_run on the state.  Every fused-block
+ * launch reads and writes the whole state once (one HBM pass); a per-gate
+ * launch reads and writes the amplitudes its gate changes. */
+typedef struct {
+  int64_t fused_launches;  /* fused-block kernels (one HBM pass each) */
+  int64_t gate_launches;   /* gates run on the per-gate kernels */
+  int64_t reserved[6];
+} qs_run_stats;
+qs_status qs_last_run_stats(qs_state s, qs_run_stats* out);
+
 /* Autotuner for fusion: run circuit c on s with every fusion setting
  * (max_fuse 1..6, which also sets the tile shape: 2^max_fuse strided chunks
  * of contiguous amplitudes), time each on the device, and remember the

@@ -132,9 +132,21 @@ qs_status qs_fuse_run(qs_state s, const qs_circuit* c, const qs_run_opts* opts) 
     qs_status st = check_gate(s, c, i);
     if (st != QS_OK) return st;
   }
+  s->run_fused_launches = 0;
+  s->run_gate_launches = 0;
   if (c->n_gates == 0) return QS_OK;
   if (max_fuse != 1) return run_fused(s, c, max_fuse == 0 ? tuned_max_fuse(s) : max_fuse);
+  s->run_gate_launches = c->n_gates;
   return qs_fuse_run_gatewise(s, c);
+}
+
+qs_status qs_last_run_stats(qs_state s, qs_run_stats* out) {
+  if (!s) return fail(QS_ERR_ARG, "state handle is NULL");
+  if (!out) return fail(QS_ERR_ARG, "out is NULL");
+  std::memset(out, 0, sizeof(*out));
+  out->fused_launches = s->run_fused_launches;
+  out->gate_launches = s->run_gate_launches;
+  return QS_OK;
 }
 
 qs_status qs_autotune(qs_state s, const qs_circuit* c, int* best_max_fuse, double* best_ms) {

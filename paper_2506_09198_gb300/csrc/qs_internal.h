@@ -23,6 +23,9 @@ struct qs_state_s {
   // Slot of this state's device-side error word (0: the shared overflow
   // slot, used once every other slot is taken).
   int err_slot = 0;
+  // Launches of the last qs_fuse_run on this state (qs_last_run_stats).
+  int64_t run_fused_launches = 0;
+  int64_t run_gate_launches = 0;
 };
 
 namespace qs {

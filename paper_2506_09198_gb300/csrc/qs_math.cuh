@@ -128,8 +128,15 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 //   value (vi, vr) by (-mi, mi): re += mr vr - mi vi, im += mr vi + mi vr.
 // Each vector term: exact product head (mul) and tail (fma against the
 // negated head), TwoSum of the head into S, every lower-order part into C.
+// A coefficient is carried as three floats, h + l + ll, which equal the
+// double exactly (24 + 24 + 24 significant bits >= 53).  With two floats a
+// coefficient keeps only ~48 bits, and that truncation is the same in every
+// application of the gate: over thousands of gates (Grover's Hadamards) it
+// adds up coherently, to several times 1e-12 against FP64.  The third part
+// costs one fma per term (ll xh; ll xl and l xl are below 2^-96 |m x|, the
+// dropped l xl below 2^-48 and of either sign).
 struct DF2Term {
-  float2 h, hn, l;  // coefficient head, negated head, tail (per channel)
+  float2 h, hn, l, ll;  // coefficient head, negated head, tail, second tail (per channel)
 };
 
 struct DF2Acc {
@@ -138,6 +145,7 @@ struct DF2Acc {
     S = mul2(a.h, xh);
     const float2 ne = fma2(a.hn, xh, S);  // S - a.h xh = -(product tail), exact
     C = sub2(fma2(a.l, xh, mul2(a.h, xl)), ne);
+    C = fma2(a.ll, xh, C);
   }
   __device__ __forceinline__ void add(const DF2Term& a, float2 xh, float2 xl) {
     const float2 pn = mul2(a.hn, xh);     // -p
@@ -149,6 +157,7 @@ struct DF2Acc {
     C = add2(C, add2(err, e));
     C = fma2(a.h, xl, C);
     C = fma2(a.l, xh, C);
+    C = fma2(a.ll, xh, C);
     S = s;
   }
 };
@@ -201,6 +210,7 @@ struct DF2AnchorAcc {
     C = add2(C, t);
     C = fma2(a.h, xl, C);
     C = fma2(a.l, xh, C);
+    C = fma2(a.ll, xh, C);
     S = s;
   }
 };
@@ -220,16 +230,21 @@ struct MathDF {
   struct Coef {
     DF2Term a, b;   // A term (mr, mr) and B term (-mi, mi)
   };
+  // h = fl(x), l = fl(x - h), ll = fl(x - h - l): each difference is exact
+  // in double, and ll holds the last <= 5 bits exactly, so h + l + ll == x.
   static __host__ Coef make_coef(double re, double im) {
     const float rh = (float)re, ih = (float)im;
     const float rl = (float)(re - (double)rh), il = (float)(im - (double)ih);
+    const float rll = (float)((re - (double)rh) - (double)rl), ill = (float)((im - (double)ih) - (double)il);
     Coef c;
     c.a.h = make_float2(rh, rh);
     c.a.hn = make_float2(-rh, -rh);
     c.a.l = make_float2(rl, rl);
+    c.a.ll = make_float2(rll, rll);
     c.b.h = make_float2(-ih, ih);
     c.b.hn = make_float2(ih, -ih);
     c.b.l = make_float2(-il, il);
+    c.b.ll = make_float2(-ill, ill);
     return c;
   }
   static __device__ __forceinline__ Val load(const Amp& a) {

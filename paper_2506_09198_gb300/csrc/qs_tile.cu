@@ -234,6 +234,7 @@ qs_status launch_plan(qs_state s, const TilePlan<typename TP::M::Coef>& plan) {
   uint32_t* err = error_word(s);
   if (!err) return fail(QS_ERR_CUDA, "device error word unavailable");
   kern<<<grid, kTileThreads, smem, s->stream>>>((typename TP::Glob*)s->psi, plan, err);
+  ++s->run_fused_launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess)
     return fail(QS_ERR_CUDA, "k_tile launch (grid %u, smem %zu, plan %zu bytes, %d ops, L %d, m %d): %s", grid, smem,
@@ -285,7 +286,10 @@ qs_status run_blocks(qs_state s, const std::vector<FGate>& gates, int max_high) 
   // Scheduling adds at most one layout change per non-diagonal gate (weight
   // 2 in the op budget; diagonal gates weigh 1), plus one bank-friendly
   // layout before the first op and one after the last.
-  const Limits lim{kTileMaxOps - 2, std::min(kTileMaxCoefs, kTileMaxCoefBytes / (int)sizeof(Coef)), kTileMaxPermBytes};
+  // Staged plans keep their coefficients within kTileMaxCoefBytes of shared
+  // memory; plans read from the parameter bank take the whole pool.
+  const int max_coefs = TP::kStagePlan ? std::min(kTileMaxCoefs, kTileMaxCoefBytes / (int)sizeof(Coef)) : kTileMaxCoefs;
+  const Limits lim{kTileMaxOps - 2, max_coefs, kTileMaxPermBytes};
   const void* ptab = phase_table(s->device, TP::kPhaseFormat);
   if (!ptab) return fail(QS_ERR_CUDA, "phase tables missing on device %d", s->device);
   static thread_local std::vector<unsigned char> plan_mem[2];
@@ -333,6 +337,7 @@ qs_status run_blocks(qs_state s, const std::vector<FGate>& gates, int max_high) 
     }
     if (emitted == 0) {
       qs_status st = flush(false);
+      ++s->run_gate_launches;
       if (st == QS_OK) st = dispatch_single(s, gates[next]);
       if (st != QS_OK) return st;
       taken[next] = 1;

@@ -297,9 +297,11 @@ struct TileDF {
     c.a.h = make_float2(p.x, p.x);
     c.a.hn = make_float2(-p.x, -p.x);
     c.a.l = make_float2(p.z, p.z);
+    c.a.ll = make_float2(0.f, 0.f);
     c.b.h = make_float2(-p.y, p.y);
     c.b.hn = make_float2(p.y, -p.y);
     c.b.l = make_float2(-p.w, p.w);
+    c.b.ll = make_float2(0.f, 0.f);
     return c;
   }
   static __device__ __forceinline__ float fxor(float x, uint32_t s) { return __uint_as_float(__float_as_uint(x) ^ s); }

@@ -43,6 +43,11 @@ class qs_circuit(ctypes.Structure):
                 ("data", ctypes.POINTER(ctypes.c_double)), ("perm", ctypes.POINTER(ctypes.c_uint32))]
 
 
+class qs_run_stats(ctypes.Structure):
+    _fields_ = [("fused_launches", ctypes.c_int64), ("gate_launches", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 6)]
+
+
 class qs_run_opts(ctypes.Structure):
     _fields_ = [("max_fuse", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
@@ -86,6 +91,7 @@ _SIGS = {
     "qs_batch_launch": [_P],
     "qs_batch_destroy": [_P],
     "qs_set_wait_limit": [ctypes.c_double],
+    "qs_last_run_stats": [_P, ctypes.POINTER(qs_run_stats)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -297,6 +303,13 @@ def run_opts(max_fuse: int = 0, use_graph: int = 0):
 
 def qs_fuse_run(h, circuit: Circuit, opts: qs_run_opts | None = None):
     _check(_lib.qs_fuse_run(h, circuit.ptr, ctypes.byref(opts) if opts is not None else None))
+
+
+def qs_last_run_stats(h) -> dict:
+    """Launch counts of the last qs_fuse_run on h."""
+    st = qs_run_stats()
+    _check(_lib.qs_last_run_stats(h, ctypes.byref(st)))
+    return {"fused_launches": st.fused_launches, "gate_launches": st.gate_launches}
 
 
 def qs_autotune(h, circuit: Circuit):

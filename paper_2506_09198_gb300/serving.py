@@ -40,6 +40,7 @@ class Request:
     arrival: float = 0.0          # seconds on the server clock
     kind: str = ""
     result_qubits: int = 8
+    meta: dict = field(default_factory=dict)  # generator parameters (marked item, basis state, ...)
     # filled by the server
     admitted: float = -1.0
     finished: float = -1.0
@@ -250,13 +251,19 @@ class Server:
             self._start_read(a, self.free_slots.pop())
         self._collect(clock)
 
-    def run(self, clock=None) -> List[Request]:
-        """Serve every submitted request; arrivals are honoured against
-        ``clock`` (seconds, default: wall time since this call)."""
+    def run(self, clock=None, admit_until: Optional[float] = None) -> List[Request]:
+        """Serve the submitted requests; arrivals are honoured against
+        ``clock`` (seconds, default: wall time since this call).  With
+        ``admit_until``, requests not admitted by then are dropped (left in
+        ``self.dropped``) and the ones already admitted run to completion."""
         t0 = time.perf_counter()
         clock = clock or (lambda: time.perf_counter() - t0)
+        self.dropped: List[Request] = []
         while self.pending or self.active or self.reading:
             now = clock()
+            if admit_until is not None and now >= admit_until and self.pending:
+                self.dropped.extend(r for _, _, r in self.pending)
+                self.pending = []
             self._admit(now)
             if not self.active:
                 if self.reading:
@@ -295,12 +302,17 @@ def make_requests(count: int, seed: int, n_min: int = 12, n_max: int = 30, rate:
         elif r < mix[0] + mix[1]:
             x = int(rng.integers(1 << n))
             kind, gates = "qft", [W.X(q) for q in range(n) if (x >> q) & 1] + W.qft(list(range(n)))
+            meta = {"x": x}
         else:
             marked = int(rng.integers(1 << n))
-            kind, gates = "grover", W.grover(n, marked, min(W.grover_iterations(n), grover_cap))
+            iters = min(W.grover_iterations(n), grover_cap)
+            kind, gates = "grover", W.grover(n, marked, iters)
+            meta = {"marked": marked, "iterations": iters}
+        if kind == "rqc":
+            meta = {}
         if rate > 0:
             t += rng.exponential(1.0 / rate)
-        reqs.append(Request(rid=i, n=n, gates=gates, arrival=t, kind=kind))
+        reqs.append(Request(rid=i, n=n, gates=gates, arrival=t, kind=kind, meta=meta))
     return reqs
 
 
