@@ -296,6 +296,28 @@ class Circuit:
     def ptr(self):
         return ctypes.pointer(self.c)
 
+    def slice(self, first: int, count: int) -> "CircuitSlice":
+        """Gates first .. first + count - 1 as a circuit of their own: the
+        records and pools are shared (record offsets index the same pools),
+        so nothing is marshalled again."""
+        first = max(0, min(int(first), self.n_gates))
+        count = max(0, min(int(count), self.n_gates - first))
+        return CircuitSlice(self, first, count)
+
+
+class CircuitSlice:
+    """A gate range of a Circuit (keeps the parent alive)."""
+
+    def __init__(self, parent: Circuit, first: int, count: int):
+        self.parent = parent
+        rec = ctypes.cast(ctypes.byref(parent.gates, first * ctypes.sizeof(qs_gate)), ctypes.POINTER(qs_gate))
+        self.c = qs_circuit(count, rec, parent.c.data, parent.c.perm)
+        self.n_gates = count
+
+    @property
+    def ptr(self):
+        return ctypes.pointer(self.c)
+
 
 def run_opts(max_fuse: int = 0, use_graph: int = 0):
     return qs_run_opts(max_fuse, use_graph)

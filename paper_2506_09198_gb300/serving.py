@@ -60,6 +60,7 @@ class _Active:
     n_chunks: int
     pos: int = 0
     stream: object = None
+    circuit: object = None  # qs.Circuit of the whole request, marshalled at admission
 
 
 class BuddyAllocator:
@@ -160,12 +161,10 @@ class Server:
     def _n_chunks(self, gates) -> int:
         return max(1, -(-len(gates) // self.chunk_gates))
 
-    def _chunk(self, a: "_Active") -> "qs.Circuit":
-        """The request's next chunk, marshalled when it is issued: the
-        host work of one tick overlaps the device work of the previous one
-        (the library copies what it needs before the call returns)."""
-        i = a.pos * self.chunk_gates
-        return qs.Circuit(a.req.gates[i:i + self.chunk_gates])
+    def _chunk(self, a: "_Active") -> "qs.CircuitSlice":
+        """The request's next chunk: a gate-range view of the circuit that was
+        marshalled once at admission (no per-chunk marshalling)."""
+        return a.circuit.slice(a.pos * self.chunk_gates, self.chunk_gates)
 
     def _admit(self, now: float):
         while self.pending and self.pending[0][0] <= now and len(self.active) < self.max_resident:
@@ -184,7 +183,8 @@ class Server:
             st = qs.State(req.n, self.dtype, handle=h)
             qs.qs_init_basis(st.h, 0)
             req.admitted = now
-            self.active[req.rid] = _Active(req, st, off, self._n_chunks(req.gates), 0, stream)
+            self.active[req.rid] = _Active(req, st, off, self._n_chunks(req.gates), 0, stream,
+                                           qs.Circuit(req.gates))
             self.used += fp
             self.peak_used = max(self.peak_used, self.used)
 

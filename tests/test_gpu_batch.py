@@ -7,7 +7,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from gpu_common import MODES, assert_close, assert_state, mode_args, qs
+from gpu_common import MODES, arith_gates, assert_close, assert_state, c128_tol, mode_args, qs
 from pins import grover_closed_form, shor_counting_distribution
 from test_gpu_fused import mixed_circuit
 
@@ -69,15 +69,25 @@ def test_batch_grover_and_shor_pins(mode):
             meta.append(("shor", n, prm, None, gates))
         circuits.append(q.Circuit(gates))
     q.qs_batch_run([s.h for s in states], circuits, q.run_opts(use_graph=1))
+    math_mode = "fp64" if mode == "c128_fp64" else "df"
     for st, m in zip(states, meta):
         got = st.read()
         ref = O.run_circuit(O.basis_state(m[1]), m[4])
-        assert_state(got, ref, mode, f"{m[0]} n={m[1]}")
+        if mode.startswith("c128"):
+            # Grover runs 25..100 iterations (up to 2.8k Hadamards per
+            # amplitude): the depth term of the tolerance applies
+            tol = c128_tol(m[4], math_mode)
+            err = float(np.max(np.abs(got - ref)))
+            assert err <= tol, f"{m[0]} n={m[1]}: max abs error {err:.3e} > {tol:.3e}"
+        else:
+            assert_state(got, ref, mode, f"{m[0]} n={m[1]}")
         if m[0] == "grover":
-            _, n, marked, r, _ = m
-            # the FP64 oracle itself is within 2.5e-13 of the closed form here
+            _, n, marked, r, gates = m
+            # the FP64 oracle itself drifts from the closed form by up to
+            # 2^-52 per Hadamard (its 1/sqrt 2 is a rounded double)
             if mode.startswith("c128"):
-                assert np.max(np.abs(got - grover_closed_form(n, marked, r))) < 1e-12
+                tol = c128_tol(gates, math_mode) + arith_gates(gates) * 2.0 ** -52
+                assert np.max(np.abs(got - grover_closed_form(n, marked, r))) < tol
         else:
             _, n, prm, _, _ = m
             p = st.probs(list(range(prm["t"])))

@@ -93,6 +93,28 @@ def test_circuit_marshalling_records():
             d_off += 2 * flat.size
 
 
+def test_circuit_slices_share_records_and_pools():
+    """A serving chunk is a gate-range view: its records are the parent's,
+    its pools the parent's (record offsets index the whole circuit's pools)."""
+    pytest.importorskip("torch")
+    try:
+        from paper_2506_09198_gb300 import qs
+    except ImportError:
+        pytest.skip("libqs not built")
+    gates = W.rqc(6, 4, seed=1) + W.shor_like(10, seed=3)[0][:5]
+    c = qs.Circuit(gates)
+    addr = lambda p: ctypes.cast(p, ctypes.c_void_p).value  # noqa: E731
+    for first, count in ((0, 4), (5, 7), (c.n_gates - 3, 10), (c.n_gates, 5)):
+        s = c.slice(first, count)
+        want = max(0, min(count, c.n_gates - first))
+        assert s.n_gates == want and s.c.n_gates == want
+        assert addr(s.c.data) == addr(c.c.data) and addr(s.c.perm) == addr(c.c.perm)
+        for j in range(want):
+            a, b = c.gates[first + j], s.c.gates[j]
+            assert (a.kind, a.k, a.ctrl_mask, a.offset) == (b.kind, b.k, b.ctrl_mask, b.offset)
+            assert list(a.targets) == list(b.targets)
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
