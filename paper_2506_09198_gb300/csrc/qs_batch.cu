@@ -48,15 +48,19 @@ struct BatchBlock {
 
 // A work item: blocks block0 .. block0 + nblocks - 1 of one state, in
 // order; of each block only tiles tau0 .. tau1 - 1 (clamped to its count).
+// resident: the state is one tile under every block: it is loaded once,
+// all its blocks run on it in shared memory, and it is stored once.
 struct BatchState {
   void* psi;
   uint32_t block0, nblocks;
   uint64_t tau0, tau1;
+  uint32_t resident;
+  uint32_t pad;
 };
 
 struct TileDesc {
   uint32_t block;   // 0xFFFFFFFF: no more work
-  uint32_t pad;
+  uint32_t nchain;  // blocks block .. block + nchain - 1 run on this tile
   uint64_t tau;
 };
 
@@ -143,6 +147,30 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_batch(const Batc
       const uint32_t si = atomicAdd(a.counter, 1u);
       if (si >= a.n_states) break;
       const BatchState st = a.states[si];
+      if (st.resident) {
+        // One tile under every block: one load, the whole chain of blocks on
+        // the consumers' side, one store (release() stores with the last
+        // block's geometry, which is the first's: L = n, m = 0).
+        const BatchBlock& b = a.blocks[st.block0];
+        const uint32_t tile_bytes = (uint32_t)sizeof(Glob) << b.L;
+        const int s = (int)(j % kStages);
+        if (!release(s)) {
+          ok = false;
+          break;
+        }
+        desc[s].block = st.block0;
+        desc[s].nchain = st.nblocks;
+        desc[s].tau = 0;
+        pending[s] = true;
+        pend_block[s] = st.block0 + st.nblocks - 1;
+        pend_j[s] = j;
+        pend_tau[s] = 0;
+        pend_psi[s] = reinterpret_cast<Glob*>(st.psi);
+        mbar_expect_tx(&full[s], tile_bytes);
+        bulk_load(smem + (size_t)s * kMaxTileBytes, st.psi, tile_bytes, &full[s]);
+        ++j;
+        continue;
+      }
       for (uint32_t bi = st.block0; bi < st.block0 + st.nblocks && ok; ++bi) {
         // Blocks of one state overlap in memory: finish the previous block.
         if (bi != st.block0 && !drain()) {
@@ -160,6 +188,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_batch(const Batc
             break;
           }
           desc[s].block = bi;
+          desc[s].nchain = 1;
           desc[s].tau = tau;
           pending[s] = true;
           pend_block[s] = bi;
@@ -207,32 +236,37 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_batch(const Batc
     if (consumers_any(!ok)) break;
     const TileDesc d = desc[s];
     if (d.block == 0xFFFFFFFFu) break;
-    const BatchBlock& b = a.blocks[d.block];
-    const TileOp* ops = a.ops + b.op0;
-    const Coef* coefs = a.coefs + b.coef0;
-    if (TP::kStagePlan && b.nops * sizeof(TileOp) + b.ncoefs * sizeof(Coef) <= kStageBytes) {
-      Coef* s_coefs = reinterpret_cast<Coef*>(s_ops + b.nops);
-      if (d.block != staged) {  // uniform: every consumer reads the same descriptor
-        consumers_sync();       // the previous block's plan is no longer read
-        const uint4* so = reinterpret_cast<const uint4*>(ops);
-        uint4* dst = reinterpret_cast<uint4*>(s_ops);
-        const int n_op16 = b.nops * (int)(sizeof(TileOp) / 16);
-        for (int i = tid; i < n_op16; i += kTileConsumers) dst[i] = so[i];
-        const uint4* sc = reinterpret_cast<const uint4*>(coefs);
-        uint4* dc = reinterpret_cast<uint4*>(s_coefs);
-        const int n_cf16 = (int)(b.ncoefs * sizeof(Coef) / 16);
-        for (int i = tid; i < n_cf16; i += kTileConsumers) dc[i] = sc[i];
-        consumers_sync();
-        staged = d.block;
-      }
-      ops = s_ops;
-      coefs = s_coefs;
-    }
-    const uint32_t tile_amps = 1u << (b.L + b.m);
     Sm* t = reinterpret_cast<Sm*>(smem + (size_t)s * kMaxTileBytes);
-    const uint64_t base = tile_base(d.tau, b.L, b.m, b.base_high);
-    consume_tile<TP>(reinterpret_cast<unsigned char*>(t), ops, b.nops, coefs, a.perm + b.perm0, b.fmt, a.phase_tab,
-                     b.L + b.m, base, tid);
+    for (uint32_t bi = d.block; bi < d.block + d.nchain; ++bi) {
+      const BatchBlock& b = a.blocks[bi];
+      const TileOp* ops = a.ops + b.op0;
+      const Coef* coefs = a.coefs + b.coef0;
+      if (TP::kStagePlan && b.nops * sizeof(TileOp) + b.ncoefs * sizeof(Coef) <= kStageBytes) {
+        Coef* s_coefs = reinterpret_cast<Coef*>(s_ops + b.nops);
+        if (bi != staged) {  // uniform: every consumer reads the same descriptor
+          consumers_sync();  // the previous block's plan (and tile) are no longer read
+          const uint4* so = reinterpret_cast<const uint4*>(ops);
+          uint4* dst = reinterpret_cast<uint4*>(s_ops);
+          const int n_op16 = b.nops * (int)(sizeof(TileOp) / 16);
+          for (int i = tid; i < n_op16; i += kTileConsumers) dst[i] = so[i];
+          const uint4* sc = reinterpret_cast<const uint4*>(coefs);
+          uint4* dc = reinterpret_cast<uint4*>(s_coefs);
+          const int n_cf16 = (int)(b.ncoefs * sizeof(Coef) / 16);
+          for (int i = tid; i < n_cf16; i += kTileConsumers) dc[i] = sc[i];
+          consumers_sync();
+          staged = bi;
+        } else if (bi != d.block) {
+          consumers_sync();  // the previous block's writes to the tile are complete
+        }
+        ops = s_ops;
+        coefs = s_coefs;
+      } else if (bi != d.block) {
+        consumers_sync();
+      }
+      const uint64_t base = tile_base(d.tau, b.L, b.m, b.base_high);
+      consume_tile<TP>(reinterpret_cast<unsigned char*>(t), ops, b.nops, coefs, a.perm + b.perm0, b.fmt,
+                       a.phase_tab, b.L + b.m, base, tid);
+    }
     fence_async_smem();
     mbar_arrive(&done[s]);
   }
@@ -271,8 +305,11 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
                         cudaStream_t stream) {
   using Coef = typename TP::M::Coef;
   const int min_chunk = sizeof(typename TP::Glob) == 16 ? 3 : 4;
-  const Limits lim{1 << 20, 65535, 65535};
+  // Every block's plan fits the shared-memory staging area, as in k_tile
+  // (a state that is one tile runs its blocks back to back on the tile).
+  const Limits lim{kTileMaxOps - 2, std::min(kTileMaxCoefs, kTileMaxCoefBytes / (int)sizeof(Coef)), kTileMaxPermBytes};
   std::vector<BatchState> bstates(count);
+  std::memset(bstates.data(), 0, bstates.size() * sizeof(BatchState));
   std::vector<BatchBlock> blocks;
   std::vector<TileOp> ops;
   std::vector<Coef> coefs;
@@ -285,7 +322,9 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
     std::vector<FGate> gates;
     gates.reserve((size_t)c->n_gates);
     for (int64_t g = 0; g < c->n_gates; ++g) gates.push_back(normalise(c, c->gates[g]));
-    MatFuser mf;  // fused matrices live until this state's blocks are copied out
+    XPusher xp;   // conjugated tables and fused matrices live until this
+    gates = xp.run(gates);
+    MatFuser mf;  // state's blocks are copied out
     gates = mf.run(gates);
     bstates[i].psi = s->psi;
     bstates[i].block0 = (uint32_t)blocks.size();
@@ -300,7 +339,7 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
       }
       Geom geom;
       const std::vector<size_t> members =
-          choose_block(gates, taken, next, s->n, TP::kTileLog, kTileMaxHigh, min_chunk, lim, 1 << 16, &geom);
+          choose_block(gates, taken, next, s->n, TP::kTileLog, kTileMaxHigh, min_chunk, lim, 512, &geom);
       if (members.empty()) return fail(QS_ERR_UNSUPPORTED, "batch state %d: gate %zu fits no tile", i, next);
       PlanBuilder<typename TP::M> pb(&bo, geom, lim);
       size_t emitted = 0;
@@ -313,6 +352,9 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
       if (bo.ops.empty()) continue;
       group_terms(bo.ops);
       bo.ops = schedule_layouts(bo.ops, geom.L + geom.m, TP::kRegBits, TP::kBankBits);
+      if (bo.ops.size() > (size_t)kTileMaxOps)
+        return fail(QS_ERR_UNSUPPORTED, "batch state %d: fused block of %zu ops exceeds %d", i, bo.ops.size(),
+                    kTileMaxOps);
       BatchBlock b;
       std::memset(&b, 0, sizeof(b));
       b.L = geom.L;
@@ -336,7 +378,7 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
     bstates[i].nblocks = (uint32_t)blocks.size() - bstates[i].block0;
     // Float-float policies keep the state in (head, tail) form between its
     // blocks: the first block reads doubles, the last writes them.
-    if (std::is_same<TP, TileDF>::value)
+    if (std::is_same<typename TP::M, MathDF>::value)
       for (uint32_t k = 0; k < bstates[i].nblocks; ++k)
         blocks[bstates[i].block0 + k].fmt =
             (k > 0 ? kTileInFF : 0) | (k + 1 < bstates[i].nblocks ? kTileOutFF : 0);
@@ -355,7 +397,10 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
   }
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
   std::vector<BatchState> sorted;
-  for (int i : order) sorted.push_back(bstates[i]);
+  for (int i : order) {
+    sorted.push_back(bstates[i]);
+    sorted.back().resident = 1;
+  }
   uint32_t nsteps = 0;
   for (int i : multi) nsteps = std::max(nsteps, bstates[i].nblocks);
   const uint64_t grid_est = (uint64_t)sm_count(states[0]->device) * kTileMinCtas;
@@ -379,6 +424,7 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
       const uint64_t nt = blocks[bstates[i].block0 + k].n_tiles;
       for (uint64_t t0 = 0; t0 < nt; t0 += per) {
         BatchState w = bstates[i];
+        w.resident = 0;
         w.block0 = bstates[i].block0 + k;
         w.nblocks = 1;
         w.tau0 = t0;
@@ -636,7 +682,7 @@ qs_status batch_run(qs_state* states, const qs_circuit* const* circuits, int cou
   const qs_state s0 = states[0];
   if (s0->dtype == QS_C64) return run_batch<TileF32Batch>(states, circuits, count, opts);
   if (s0->math == QS_MATH_FP64) return run_batch<TileF64>(states, circuits, count, opts);
-  return run_batch<TileDF>(states, circuits, count, opts);
+  return run_batch<TileDFBatch>(states, circuits, count, opts);
 }
 
 }  // namespace qs
@@ -706,7 +752,7 @@ qs_status qs_batch_compile(qs_state* states, const qs_circuit* const* circuits, 
   else if (s0->math == QS_MATH_FP64)
     st = compile_handle<TileF64>(b, states, circuits, count);
   else
-    st = compile_handle<TileDF>(b, states, circuits, count);
+    st = compile_handle<TileDFBatch>(b, states, circuits, count);
   if (st == QS_OK) {
     // The workspace copy is queued on the first state's stream; the graph
     // is launched there too, so it is ordered after the copy.

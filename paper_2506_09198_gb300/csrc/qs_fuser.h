@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <deque>
 #include <functional>
 #include <vector>
 
@@ -52,9 +53,13 @@ inline uint8_t row_exp_biased(const double* U, int row, int dim) {
   return (uint8_t)(e + 128);
 }
 
+// Internal gate kind (never in a qs_circuit): multiply the amplitudes whose
+// bits under pmask equal ppat by the complex number at data.
+constexpr int kGatePattern = 100;
+
 // One gate record in normalised form.
 struct FGate {
-  int kind;  // QS_GATE_*
+  int kind;  // QS_GATE_* or kGatePattern
   int k;
   int targets[QS_MAX_TARGETS];
   uint64_t ctrl;
@@ -63,6 +68,7 @@ struct FGate {
   bool diagonal;        // needs no tile qubits
   uint64_t qubit_mask;  // targets | controls
   uint64_t tmask;       // targets that must be tile qubits
+  uint64_t pmask, ppat;  // kGatePattern
 };
 
 inline bool matrix_is_diag(const double* M, int dim) {
@@ -94,9 +100,142 @@ inline FGate normalise(const qs_circuit* c, const qs_gate& g) {
   return f;
 }
 
+// Uncontrolled X given as a 2x2 matrix or a one-qubit permutation.
+inline bool is_plain_x(const FGate& g) {
+  if (g.ctrl != 0 || g.k != 1) return false;
+  if (g.kind == QS_GATE_PERM) return g.perm[0] == 1u && g.perm[1] == 0u;
+  if (g.kind == QS_GATE_U1)
+    return is_c(g.data, 0, 0) && is_c(g.data + 2, 1, 0) && is_c(g.data + 4, 1, 0) && is_c(g.data + 6, 0, 0);
+  return false;
+}
+
+// Diagonal entry v of a diagonal gate (DIAG table, or the diagonal of a
+// U1 / UK matrix).
+inline const double* diag_entry(const FGate& g, int v) {
+  if (g.kind == QS_GATE_DIAG) return g.data + 2 * v;
+  const int dim = 1 << g.k;
+  return g.data + 2 * (v * dim + v);
+}
+
+// Moves uncontrolled X gates later in the circuit past diagonal gates, which
+// they conjugate (X_q D = D' X_q, D' = D with index bit q flipped), so that
+// two X on one qubit cancel.  An X-conjugated multi-controlled phase (a
+// Grover oracle or diffusion core) becomes one phase on a bit pattern that
+// needs no tile qubits.  A pending X is emitted before the first gate that
+// is not diagonal on its qubit (or that this pass cannot conjugate), and at
+// the end.  Moves and phases are exact, so the circuit's arithmetic is
+// unchanged.  The tables and coefficients it creates live in this object.
+class XPusher {
+ public:
+  std::vector<FGate> run(const std::vector<FGate>& in) {
+    std::vector<FGate> out;
+    out.reserve(in.size());
+    uint64_t pend = 0;
+    auto flush = [&](uint64_t qm) {
+      const uint64_t f = qm & pend;
+      for (int q = 0; q < 64; ++q)
+        if ((f >> q) & 1ull) out.push_back(make_x(q));
+      pend &= ~qm;
+    };
+    for (const FGate& g : in) {
+      if (is_plain_x(g)) {
+        pend ^= 1ull << g.targets[0];
+        continue;
+      }
+      const uint64_t hit = g.qubit_mask & pend;
+      if (!hit) {
+        out.push_back(g);
+        continue;
+      }
+      if (g.diagonal && g.kind != kGatePattern) {
+        const int dim = 1 << g.k;
+        int n_other = 0, v_other = 0;
+        for (int v = 0; v < dim; ++v)
+          if (!is_c(diag_entry(g, v), 1, 0)) {
+            ++n_other;
+            v_other = v;
+          }
+        if (n_other == 0) continue;  // identity
+        uint64_t tbits = 0, vbits = 0;
+        for (int j = 0; j < g.k; ++j) {
+          tbits |= 1ull << g.targets[j];
+          if ((v_other >> j) & 1) vbits |= 1ull << g.targets[j];
+        }
+        if (n_other == 1) {
+          const uint64_t mask = tbits | g.ctrl;
+          out.push_back(make_pattern(mask, (vbits | g.ctrl) ^ hit, diag_entry(g, v_other)));
+          continue;
+        }
+        if ((hit & g.ctrl) == 0) {
+          // X on targets: the table's index bits flip
+          uint32_t flip = 0;
+          for (int j = 0; j < g.k; ++j)
+            if ((hit >> g.targets[j]) & 1ull) flip |= 1u << j;
+          store_.emplace_back(2 * dim);
+          std::vector<double>& t = store_.back();
+          for (int v = 0; v < dim; ++v) {
+            const double* e = diag_entry(g, v ^ (int)flip);
+            t[2 * v] = e[0];
+            t[2 * v + 1] = e[1];
+          }
+          FGate d = g;
+          d.kind = QS_GATE_DIAG;
+          d.data = t.data();
+          out.push_back(d);
+          continue;
+        }
+      }
+      if (g.kind == kGatePattern) {
+        FGate p = g;
+        p.ppat ^= hit;
+        out.push_back(p);
+        continue;
+      }
+      flush(g.qubit_mask);
+      out.push_back(g);
+    }
+    flush(~0ull);
+    return out;
+  }
+
+ private:
+  std::deque<std::vector<double>> store_;
+  static constexpr uint32_t kXPerm[2] = {1u, 0u};
+
+  static FGate blank() {
+    FGate f;
+    std::memset(&f, 0, sizeof(f));
+    return f;
+  }
+  FGate make_x(int q) const {
+    FGate f = blank();
+    f.kind = QS_GATE_PERM;
+    f.k = 1;
+    f.targets[0] = q;
+    f.perm = kXPerm;
+    f.qubit_mask = 1ull << q;
+    f.tmask = 1ull << q;
+    return f;
+  }
+  FGate make_pattern(uint64_t mask, uint64_t pattern, const double* c) {
+    store_.emplace_back(2);
+    store_.back()[0] = c[0];
+    store_.back()[1] = c[1];
+    FGate f = blank();
+    f.kind = kGatePattern;
+    f.data = store_.back().data();
+    f.diagonal = true;
+    f.qubit_mask = mask;
+    f.pmask = mask;
+    f.ppat = pattern;
+    return f;
+  }
+};
+
 // Gates a tile op can express: dense matrices on at most 2 targets,
 // diagonals and permutations on at most 8.
 inline bool tileable(const FGate& g) {
+  if (g.kind == kGatePattern) return true;
   if (g.kind == QS_GATE_DIAG || g.kind == QS_GATE_PERM || g.diagonal) return g.k <= 8;
   return g.k <= 2;
 }
@@ -319,6 +458,7 @@ struct PlanBuilder {
 
   // Translate one gate; false if the block has no room for it.
   bool add(const FGate& g) {
+    if (g.kind == kGatePattern) return phase(g.pmask, g.ppat, g.data);
     if (g.kind == QS_GATE_DIAG) return diag(g.targets, g.k, g.ctrl, g.data);
     if (g.kind == QS_GATE_PERM) {
       bool ident = true;
@@ -567,7 +707,9 @@ inline int op_weight(const FGate& g) { return g.diagonal ? 1 : 2; }
 inline void pool_need(const FGate& g, int* coefs, int* perm_bytes) {
   *coefs = 0;
   *perm_bytes = 0;
-  if (g.kind == QS_GATE_PERM)
+  if (g.kind == kGatePattern)
+    *coefs = 1;
+  else if (g.kind == QS_GATE_PERM)
     *perm_bytes = 1 << g.k;
   else if (g.kind == QS_GATE_DIAG || g.diagonal)
     *coefs = 1 << g.k;

@@ -117,7 +117,7 @@ __global__ void QS_DENSE1_BOUNDS k_dense1(typename P::Amp* __restrict__ psi, uin
       if (item < n_items) {
         iu[u] = expand_index(item, ins);
         a[u] = psi[iu[u]];
-        b[u] = psi[iu[u] | tbit];
+        b[u] = psi[iu[u] ^ tbit];
       }
     }
 #pragma unroll
@@ -171,7 +171,7 @@ __global__ void QS_DENSE2_BOUNDS k_dense2(typename P::Amp* __restrict__ psi, uin
         // rows keep TwoSum, which stays exact when heads cancel (structured
         // states such as Grover's, where every pair computes the same values
         // and rounding errors would add coherently).
-        if constexpr (std::is_same<P, MathDF>::value) {
+        if constexpr (std::is_same<P, MathDFGate>::value) {
           const int mexp = P::template max_exp_field<4>(v);
           psi[i0[u]] = P::template mac_anchor_round<4>(&g.m[0], v, g.row_exp[0], mexp);
           psi[i0[u] | b0] = P::template mac_anchor_round<4>(&g.m[4], v, g.row_exp[1], mexp);
@@ -222,6 +222,9 @@ __global__ void __launch_bounds__(kThreads) k_phase(typename P::Amp* __restrict_
 }
 
 // X: swap partners.  Y: up' = -i lo, lo' = i up (moves and sign flips only).
+// The partner of index i is i ^ tbit: for X and Y tbit is the target bit (0
+// in i); a transposition of two sub-register values p <-> q (SWAP) has i on
+// p and tbit = the index bits where p and q differ.
 template <class Amp, bool Y, int ILP>
 __global__ void __launch_bounds__(kThreads) k_xy(Amp* __restrict__ psi, uint64_t n_items, uint64_t tbit,
                                                  DevInsert ins) {
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(kThreads) k_xy(Amp* __restrict__ psi, uint64_t
       if (item < n_items) {
         iu[u] = expand_index(item, ins);
         a[u] = psi[iu[u]];
-        b[u] = psi[iu[u] | tbit];
+        b[u] = psi[iu[u] ^ tbit];
       }
     }
 #pragma unroll
@@ -249,10 +252,10 @@ __global__ void __launch_bounds__(kThreads) k_xy(Amp* __restrict__ psi, uint64_t
           lo.x = neg_s(a[u].y);     //  i (x + iy) = -y + ix
           lo.y = a[u].x;
           psi[iu[u]] = up;
-          psi[iu[u] | tbit] = lo;
+          psi[iu[u] ^ tbit] = lo;
         } else {
           psi[iu[u]] = b[u];
-          psi[iu[u] | tbit] = a[u];
+          psi[iu[u] ^ tbit] = a[u];
         }
       }
     }
@@ -272,6 +275,13 @@ template <class P, int ILP>
 __global__ void __launch_bounds__(kThreads) k_diag(typename P::Amp* __restrict__ psi, uint64_t n_items,
                                                    DevInsert ins, const __grid_constant__ DiagTable<P> tab) {
   using Amp = typename P::Amp;
+  using Coef = typename P::Coef;
+  // Lanes read different entries: gathered from the parameter bank they
+  // would serialise, so the table is staged in shared memory first.
+  __shared__ __align__(16) unsigned char s_raw[sizeof(Coef) * kMaxDiag];
+  Coef* s_d = reinterpret_cast<Coef*>(s_raw);
+  for (int i = threadIdx.x; i < (1 << tab.k); i += blockDim.x) s_d[i] = tab.d[i];
+  __syncthreads();
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; base < n_items; base += stride * ILP) {
     uint64_t ii[ILP];
@@ -291,7 +301,7 @@ __global__ void __launch_bounds__(kThreads) k_diag(typename P::Amp* __restrict__
         uint32_t sidx = 0;
         for (int j = 0; j < tab.k; ++j) sidx |= (uint32_t)((ii[u] >> tab.targets[j]) & 1u) << j;
         typename P::Val v = P::load(a[u]);
-        psi[ii[u]] = P::template mac_round<1>(&tab.d[sidx], &v);
+        psi[ii[u]] = P::template mac_round<1>(&s_d[sidx], &v);
       }
     }
   }
@@ -393,7 +403,7 @@ static qs_status dense1_impl(qs_state s, int t, uint64_t ctrl_mask, const double
 qs_status launch_dense1(qs_state s, int target, uint64_t ctrl_mask, const double* U) {
   if (s->dtype == QS_C64) return dense1_impl<MathF32>(s, target, ctrl_mask, U);
   if (s->math == QS_MATH_FP64) return dense1_impl<MathF64>(s, target, ctrl_mask, U);
-  return dense1_impl<MathDF>(s, target, ctrl_mask, U);
+  return dense1_impl<MathDFGate>(s, target, ctrl_mask, U);
 }
 
 template <class P>
@@ -413,7 +423,7 @@ static qs_status dense2_impl(qs_state s, int t0, int t1, uint64_t ctrl_mask, con
 qs_status launch_dense2(qs_state s, int t0, int t1, uint64_t ctrl_mask, const double* U) {
   if (s->dtype == QS_C64) return dense2_impl<MathF32>(s, t0, t1, ctrl_mask, U);
   if (s->math == QS_MATH_FP64) return dense2_impl<MathF64>(s, t0, t1, ctrl_mask, U);
-  return dense2_impl<MathDF>(s, t0, t1, ctrl_mask, U);
+  return dense2_impl<MathDFGate>(s, t0, t1, ctrl_mask, U);
 }
 
 template <class P>
@@ -439,7 +449,7 @@ static qs_status phase_impl(qs_state s, uint64_t mask, uint64_t pattern, double 
 qs_status launch_phase(qs_state s, uint64_t mask, uint64_t pattern, double c_re, double c_im) {
   if (s->dtype == QS_C64) return phase_impl<MathF32>(s, mask, pattern, c_re, c_im);
   if (s->math == QS_MATH_FP64) return phase_impl<MathF64>(s, mask, pattern, c_re, c_im);
-  return phase_impl<MathDF>(s, mask, pattern, c_re, c_im);
+  return phase_impl<MathDFGate>(s, mask, pattern, c_re, c_im);
 }
 
 template <class Amp>
@@ -457,6 +467,31 @@ static qs_status xy_impl(qs_state s, int t, uint64_t ctrl_mask, int y) {
     kern<<<grid, kThreads, 0, s->stream>>>((Amp*)s->psi, items, 1ull << t, ins);
   }
   return after_launch("k_xy");
+}
+
+// Exchange of the amplitudes whose sub-register on targets is p with those
+// where it is q (all other bits equal, controls 1): reads and writes only the
+// 2^(n - k - c + 1) amplitudes that move.
+template <class Amp>
+static qs_status pairswap_impl(qs_state s, const int* targets, int k, uint64_t ctrl_mask, uint32_t p, uint32_t q) {
+  constexpr int ILP = 2;
+  const uint64_t items = 1ull << (s->n - k - popcount64(ctrl_mask));
+  uint64_t pbits = 0, qbits = 0;
+  for (int j = 0; j < k; ++j) {
+    if ((p >> j) & 1u) pbits |= 1ull << targets[j];
+    if ((q >> j) & 1u) qbits |= 1ull << targets[j];
+  }
+  std::vector<int> pos(targets, targets + k);
+  DevInsert ins = to_dev(make_insert(with_ctrls(pos, ctrl_mask), ctrl_mask | pbits));
+  auto kern = k_xy<Amp, false, ILP>;
+  unsigned grid = grid_for(kern, items, ILP, s->device);
+  kern<<<grid, kThreads, 0, s->stream>>>((Amp*)s->psi, items, pbits ^ qbits, ins);
+  return after_launch("k_xy");
+}
+
+qs_status launch_pairswap(qs_state s, const int* targets, int k, uint64_t ctrl_mask, uint32_t p, uint32_t q) {
+  if (s->dtype == QS_C64) return pairswap_impl<float2>(s, targets, k, ctrl_mask, p, q);
+  return pairswap_impl<double2>(s, targets, k, ctrl_mask, p, q);
 }
 
 qs_status launch_xy(qs_state s, int target, uint64_t ctrl_mask, int y) {
@@ -486,7 +521,7 @@ static qs_status diag_impl(qs_state s, const int* targets, int k, uint64_t ctrl_
 qs_status launch_diag(qs_state s, const int* targets, int k, uint64_t ctrl_mask, const double* d) {
   if (s->dtype == QS_C64) return diag_impl<MathF32>(s, targets, k, ctrl_mask, d);
   if (s->math == QS_MATH_FP64) return diag_impl<MathF64>(s, targets, k, ctrl_mask, d);
-  return diag_impl<MathDF>(s, targets, k, ctrl_mask, d);
+  return diag_impl<MathDFGate>(s, targets, k, ctrl_mask, d);
 }
 
 template <class Amp>
@@ -571,6 +606,16 @@ qs_status dispatch_perm(qs_state s, const int* targets, int k, uint64_t ctrl_mas
   for (int v = 0; v < (1 << k); ++v) ident = ident && perm[v] == (uint32_t)v;
   if (ident) return QS_OK;
   if (k == 1) return launch_xy(s, targets[0], ctrl_mask, 0);
+  // A single transposition p <-> q (SWAP is 01 <-> 10) moves only its pairs.
+  int moved = 0;
+  uint32_t mp = 0, mq = 0;
+  for (int v = 0; v < (1 << k); ++v)
+    if (perm[v] != (uint32_t)v) {
+      if (moved == 0) mp = (uint32_t)v;
+      if (moved == 1) mq = (uint32_t)v;
+      ++moved;
+    }
+  if (moved == 2 && perm[mp] == mq && perm[mq] == mp) return launch_pairswap(s, targets, k, ctrl_mask, mp, mq);
   return launch_perm(s, targets, k, ctrl_mask, perm);
 }
 

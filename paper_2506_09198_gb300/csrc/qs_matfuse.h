@@ -105,7 +105,7 @@ class MatFuser {
   int owner_[64];
 
   static bool mergeable(const FGate& g) {
-    if (g.kind == QS_GATE_PERM) return false;
+    if (g.kind == QS_GATE_PERM || g.kind == kGatePattern) return false;
     if (!tileable(g)) return false;
     return __builtin_popcountll(g.qubit_mask) <= 2;
   }

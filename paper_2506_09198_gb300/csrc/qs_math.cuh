@@ -141,12 +141,15 @@ struct DF2Term {
 
 struct DF2Acc {
   float2 S, C;
+  // LL: include the coefficient's second tail (exact double coefficients).
+  template <bool LL = true>
   __device__ __forceinline__ void first(const DF2Term& a, float2 xh, float2 xl) {
     S = mul2(a.h, xh);
     const float2 ne = fma2(a.hn, xh, S);  // S - a.h xh = -(product tail), exact
     C = sub2(fma2(a.l, xh, mul2(a.h, xl)), ne);
-    C = fma2(a.ll, xh, C);
+    if (LL) C = fma2(a.ll, xh, C);
   }
+  template <bool LL = true>
   __device__ __forceinline__ void add(const DF2Term& a, float2 xh, float2 xl) {
     const float2 pn = mul2(a.hn, xh);     // -p
     const float2 e = fma2(a.h, xh, pn);   // a.h xh - p, exact
@@ -157,7 +160,7 @@ struct DF2Acc {
     C = add2(C, add2(err, e));
     C = fma2(a.h, xl, C);
     C = fma2(a.l, xh, C);
-    C = fma2(a.ll, xh, C);
+    if (LL) C = fma2(a.ll, xh, C);
     S = s;
   }
 };
@@ -203,6 +206,7 @@ struct MathF32 {
 // yields their sum rounded once: 7 packed operations per term.
 struct DF2AnchorAcc {
   float2 S, C;
+  template <bool LL = true>
   __device__ __forceinline__ void add(const DF2Term& a, float2 xh, float2 xl) {
     const float2 p = mul2(a.h, xh);
     const float2 s = add2(S, p);
@@ -210,7 +214,7 @@ struct DF2AnchorAcc {
     C = add2(C, t);
     C = fma2(a.h, xl, C);
     C = fma2(a.l, xh, C);
-    C = fma2(a.ll, xh, C);
+    if (LL) C = fma2(a.ll, xh, C);
     S = s;
   }
 };
@@ -221,7 +225,8 @@ __device__ __forceinline__ float pow2_field(int e) {
   return __uint_as_float((uint32_t)e << 23);
 }
 
-struct MathDF {
+template <bool LL>
+struct MathDFT {
   using Amp = double2;
   struct Val {
     float2 h, l;    // (re, im) heads and tails
@@ -258,12 +263,12 @@ struct MathDF {
   template <int K>
   static __device__ __forceinline__ DF2Acc mac(const Coef* m, const Val* v) {
     DF2Acc acc;
-    acc.first(m[0].a, v[0].h, v[0].l);
-    acc.add(m[0].b, v[0].hs, v[0].ls);
+    acc.template first<LL>(m[0].a, v[0].h, v[0].l);
+    acc.template add<LL>(m[0].b, v[0].hs, v[0].ls);
 #pragma unroll
     for (int k = 1; k < K; ++k) {
-      acc.add(m[k].a, v[k].h, v[k].l);
-      acc.add(m[k].b, v[k].hs, v[k].ls);
+      acc.template add<LL>(m[k].a, v[k].h, v[k].l);
+      acc.template add<LL>(m[k].b, v[k].hs, v[k].ls);
     }
     return acc;
   }
@@ -291,8 +296,8 @@ struct MathDF {
     acc.C = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      acc.add(m[k].a, v[k].h, v[k].l);
-      acc.add(m[k].b, v[k].hs, v[k].ls);
+      acc.template add<LL>(m[k].a, v[k].h, v[k].l);
+      acc.template add<LL>(m[k].b, v[k].hs, v[k].ls);
     }
     DF2Acc r;
     r.S = sub2(acc.S, make_float2(A, A));
@@ -305,5 +310,13 @@ struct MathDF {
     return make_double2(f2d_exact(acc.S.x) + f2d_exact(acc.C.x), f2d_exact(acc.S.y) + f2d_exact(acc.C.y));
   }
 };
+
+// Fused and batched tiles keep the state in float-float form across many
+// gates: exact double coefficients (three floats).
+using MathDF = MathDFT<true>;
+// Per-gate kernels round every result to IEEE double; they leave out the
+// second coefficient tail (at most 2^-49 of a coefficient, below their own
+// float-float rounding), which keeps them at the memory bound.
+using MathDFGate = MathDFT<false>;
 
 }  // namespace qs

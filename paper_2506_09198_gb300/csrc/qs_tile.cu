@@ -243,6 +243,7 @@ qs_status launch_plan(qs_state s, const TilePlan<typename TP::M::Coef>& plan) {
 }
 
 qs_status dispatch_single(qs_state s, const FGate& g) {
+  if (g.kind == kGatePattern) return launch_phase(s, g.pmask, g.ppat, g.data[0], g.data[1]);
   if (g.kind == QS_GATE_PERM) return dispatch_perm(s, g.targets, g.k, g.ctrl, g.perm);
   if (g.kind == QS_GATE_DIAG) return dispatch_diag(s, g.targets, g.k, g.ctrl, g.data);
   if (g.kind == QS_GATE_U1) return dispatch_u1(s, g.targets[0], g.ctrl, g.data);
@@ -377,6 +378,8 @@ qs_status run_fused(qs_state s, const qs_circuit* c, int max_high) {
   std::vector<FGate> gates;
   gates.reserve((size_t)c->n_gates);
   for (int64_t i = 0; i < c->n_gates; ++i) gates.push_back(normalise(c, c->gates[i]));
+  XPusher xp;   // owns conjugated tables until the blocks are launched
+  gates = xp.run(gates);
   MatFuser mf;  // owns the fused matrices until the blocks are launched
   gates = mf.run(gates);
   if (max_high > kTileMaxHigh) max_high = kTileMaxHigh;

@@ -103,6 +103,8 @@ __device__ __forceinline__ bool consumers_any(bool v) {
 // ---------------------------------------------------------------------------
 struct TileF32 {
   using M = MathF32;
+  // Copy a 2x2 op's four coefficients to registers before the pairs.
+  static constexpr bool kHoistCoefs = true;
   // Uncontrolled 4x4 ops take the quads two at a time (one coefficient load
   // serves both); the batched kernel, with more live state, opts out.
   static constexpr bool kQuadPairs = true;
@@ -183,6 +185,7 @@ __device__ __forceinline__ double dneg(double x) {
 
 struct TileF64 {
   using M = MathF64;
+  static constexpr bool kHoistCoefs = true;
   static constexpr bool kQuadPairs = false;
   // Stage the block's ops and coefficients in shared memory.
   static constexpr bool kStagePlan = true;
@@ -228,9 +231,12 @@ struct TileF64 {
 struct TileDF {
   using M = MathDF;
   static constexpr bool kQuadPairs = false;
-  // The float-float plan stays in the parameter bank: staged in shared
-  // memory, the compiler keeps more of it live and spills.
-  static constexpr bool kStagePlan = false;
+  // Plans are staged in shared memory: the lanes of a diagonal op gather
+  // different coefficients, which the parameter bank would serialise.
+  static constexpr bool kStagePlan = true;
+  // A float-float coefficient is 64 bytes: a 2x2 op reads its coefficients
+  // from the staged plan where it uses them rather than holding all four.
+  static constexpr bool kHoistCoefs = false;
   using Glob = double2;
   using Sm = float4;
   static constexpr int kTileLog = 11;
@@ -309,6 +315,9 @@ struct TileDF {
     return make_float4(fxor(a.x, s), fxor(a.y, s), fxor(a.z, s), fxor(a.w, s));
   }
 };
+
+// The batched kernel stages float-float plans like k_tile does.
+using TileDFBatch = TileDF;
 
 // ---------------------------------------------------------------------------
 // Register-resident tile consumer
@@ -439,9 +448,12 @@ struct RegTile {
 
   template <int K, bool CTRL, bool REAL>
   __device__ __forceinline__ void dense1(const Coef* cf, uint32_t lmask) {
-    Coef c[4];
+    Coef hc[TP::kHoistCoefs ? 4 : 1];
+    if constexpr (TP::kHoistCoefs) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) c[j] = cf[j];
+      for (int j = 0; j < 4; ++j) hc[j] = cf[j];
+    }
+    const Coef* c = TP::kHoistCoefs ? hc : cf;
     // 2x2 rows keep TwoSum accumulation (exact under cancellation).
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -543,15 +555,29 @@ struct RegTile {
   }
 
   __device__ __forceinline__ void diag(const TileOp& op, const Coef* cf, uint64_t base) {
+    // Table index s = (tile bits) | (thread bits) | (register bits): the
+    // first two are fixed for the thread, the register part is the OR of
+    // the entries of the register's set bits, found once per op.
     uint32_t sg = 0;
     for (int j = 0; j < op.k; ++j)
       if (op.gq[j] != 0xFF) sg |= (uint32_t)((base >> op.gq[j]) & 1ull) << j;
+    uint32_t rbit[RB];
+#pragma unroll
+    for (int b = 0; b < RB; ++b) rbit[b] = 0u;
+    for (int j = 0; j < op.nloc; ++j) {
+      const uint32_t lb = 1u << op.tpos[j], sb = 1u << op.tj[j];
+      if (toff & lb) sg |= sb;
+#pragma unroll
+      for (int b = 0; b < RB; ++b) rbit[b] |= pbit[b] == lb ? sb : 0u;
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const uint32_t lam = toff | roff(r);
       if ((lam & op.lmask) != op.lmask) continue;
       uint32_t sidx = sg;
-      for (int j = 0; j < op.nloc; ++j) sidx |= ((lam >> op.tpos[j]) & 1u) << op.tj[j];
+#pragma unroll
+      for (int b = 0; b < RB; ++b)
+        if ((r >> b) & 1) sidx |= rbit[b];
       const Val x = TP::val(v[r]);
       v[r] = TP::template mac<1>(cf + sidx, &x);
     }

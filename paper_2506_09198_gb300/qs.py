@@ -296,6 +296,39 @@ class Circuit:
     def ptr(self):
         return ctypes.pointer(self.c)
 
+    @classmethod
+    def repeated(cls, parts) -> "Circuit":
+        """A circuit made of parts [(gates, count), ...]: each part's gates
+        repeated count times, in order (Grover iterations, Trotter steps).
+        Each part is marshalled once and its records are tiled; every copy
+        refers to the same matrices and tables in the pools."""
+        subs = [(cls(list(g)), int(cnt)) for g, cnt in parts if cnt > 0 and len(g) > 0]
+        self = cls.__new__(cls)
+        rec_size = ctypes.sizeof(qs_gate)
+        chunks, data, perm = [], [], []
+        nd = npm = 0
+        for c, cnt in subs:
+            raw = np.frombuffer(ctypes.string_at(ctypes.addressof(c.gates), c.n_gates * rec_size), dtype=np.uint8)
+            recs = raw.reshape(c.n_gates, rec_size).copy()
+            off = recs[:, 48:56].copy().view(np.int64).reshape(-1)
+            kind = recs[:, 0:4].copy().view(np.int32).reshape(-1)
+            off = np.where(kind == QS_GATE_PERM, off + npm, off + nd)
+            recs[:, 48:56] = off.astype(np.int64).view(np.uint8).reshape(-1, 8)
+            chunks.append(np.tile(recs, (cnt, 1)))
+            data.append(c.data)
+            perm.append(c.perm)
+            nd += c.data.size
+            npm += c.perm.size
+        allrec = np.ascontiguousarray(np.concatenate(chunks) if chunks else np.zeros((1, rec_size), np.uint8))
+        n = int(sum(c.n_gates * cnt for c, cnt in subs))
+        self._rec_buf = allrec
+        self.gates = (qs_gate * max(1, n)).from_buffer(allrec)
+        self.data = np.ascontiguousarray(np.concatenate(data) if data else np.zeros(2))
+        self.perm = np.ascontiguousarray(np.concatenate(perm) if perm else np.zeros(1, dtype=np.uint32))
+        self.c = qs_circuit(n, self.gates, self.data.ctypes.data_as(_PD), self.perm.ctypes.data_as(_PU32))
+        self.n_gates = n
+        return self
+
     def slice(self, first: int, count: int) -> "CircuitSlice":
         """Gates first .. first + count - 1 as a circuit of their own: the
         records and pools are shared (record offsets index the same pools),

@@ -130,6 +130,66 @@ def test_fused_grover_success_probability(mode):
         assert fidelity(got, grover_closed_form(n, marked, r)) >= 1 - 1e-5
 
 
+def x_diag_circuit(n, n_gates, seed):
+    """X gates around diagonal gates of every form (phase on one pattern,
+    general diagonal tables, controls on X'd qubits), with H and CNOT
+    between them: the fuser moves X gates past the diagonals it can
+    conjugate and cancels pairs."""
+    rng = W.rng_for(seed)
+    gates = []
+    for _ in range(n_gates):
+        r = rng.random()
+        if r < 0.35:
+            gates.append(W.X(int(rng.integers(n))))
+        elif r < 0.5:
+            q = W.random_distinct(rng, n, 3)
+            gates.append(W.MCZ(q[:2], q[2]))
+        elif r < 0.6:
+            q = W.random_distinct(rng, n, 2)
+            gates.append(W.CP(q[0], q[1], float(rng.uniform(0, 6.2))))
+        elif r < 0.72:
+            k = int(rng.integers(1, 4))
+            q = W.random_distinct(rng, n, k + 2)
+            nc = int(rng.integers(0, 3))
+            d = np.exp(1j * rng.uniform(0, 6.2, size=1 << k))
+            gates.append(W.gdiag(q[:k], d, ctrls=q[k:k + nc]))
+        elif r < 0.8:
+            gates.append(W.T(int(rng.integers(n))))
+        elif r < 0.9:
+            gates.append(W.H(int(rng.integers(n))))
+        else:
+            c, t = W.random_distinct(rng, n, 2)
+            gates.append(W.CNOT(c, t))
+    return gates
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("max_fuse", [0, 2])
+def test_x_conjugation_rewrite(mode, max_fuse):
+    for n, seed in ((6, 71), (13, 72), (17, 73)):
+        gates = x_diag_circuit(n, 160, seed)
+        psi0 = W.random_state(n, W.rng_for(seed + 1))
+        ref = O.run_circuit(psi0.copy(), gates)
+        got = run_gpu(n, mode, gates, psi0, max_fuse)
+        assert_close(got, ref, mode, f"X conjugation n={n} max_fuse={max_fuse}")
+
+
+@pytest.mark.parametrize("mode", ["c128_df", "c64"])
+def test_grover_iteration_takes_few_passes(mode):
+    """With the oracle's and the diffusion's X gates moved through their
+    multi-controlled Z, a Grover iteration on 16 qubits is two phases on a
+    bit pattern and two H layers: a handful of fused passes, not one per X
+    layer."""
+    n, marked, r = 16, 12345, 20
+    st = new_state(n, mode)
+    st.run(W.grover(n, marked, r), max_fuse=4)
+    passes = qs().qs_last_run_stats(st.h)["fused_launches"]
+    got = st.read()
+    st.close()
+    assert passes <= 3 * r + 4, f"{passes} fused passes for {r} Grover iterations"
+    assert_state(got, O.run_circuit(O.basis_state(n), W.grover(n, marked, r)), mode, "Grover 16q")
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_fused_shor_like(mode):
     n = 13

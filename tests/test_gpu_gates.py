@@ -155,6 +155,27 @@ def test_perm_k_exact(mode, k):
 
 
 @pytest.mark.parametrize("mode", MODES)
+def test_single_transpositions_exact(mode):
+    """Permutations that exchange exactly two sub-register values (SWAP is
+    01 <-> 10) run on the pair-exchange kernel: bit-exact against the oracle,
+    with and without controls, on low, high and mixed qubits."""
+    n = 13
+    rng = W.rng_for(6400)
+    gates = [W.SWAP(0, 1), W.SWAP(0, 12), W.SWAP(7, 3), W.gperm((5, 6), np.array([0, 1, 2, 3][::-1], np.uint32)),
+             W.SWAP(2, 9)]
+    gates[-1] = W.Gate("perm", (2, 9), np.array([0, 2, 1, 3], np.uint32), ctrls=(4, 11), name="cswap")
+    for k in (2, 3, 5):
+        for nc in (0, 2):
+            q = W.random_distinct(rng, n, k + nc)
+            p = np.arange(1 << k, dtype=np.uint32)
+            a, b = (int(x) for x in rng.choice(1 << k, size=2, replace=False))
+            p[a], p[b] = b, a
+            gates.append(W.gperm(q[:k], p, ctrls=q[k:]))
+    got, ref = _run_both(n, mode, gates, 6401)
+    assert np.array_equal(got, ref.astype(got.dtype)), "transpositions must move amplitudes exactly"
+
+
+@pytest.mark.parametrize("mode", MODES)
 def test_perm_whole_register(mode):
     n = 8
     rng = W.rng_for(6500)

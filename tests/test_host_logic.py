@@ -115,6 +115,33 @@ def test_circuit_slices_share_records_and_pools():
             assert list(a.targets) == list(b.targets)
 
 
+def test_repeated_circuit_equals_the_flat_one():
+    """Circuit.repeated (each part marshalled once, records tiled, pools
+    shared) gives the same gate sequence as marshalling the flat list."""
+    pytest.importorskip("torch")
+    try:
+        from paper_2506_09198_gb300 import qs
+    except ImportError:
+        pytest.skip("libqs not built")
+    n, m = 9, 300
+    r = W.grover_iterations(n)
+    shor = W.shor_like(10, seed=4)[0]
+    cases = [(W.grover(n, m), [(W.grover(n, m, 0), 1), (W.grover(n, m, 1)[n:], r)]),
+             (shor[:4] * 3 + shor[4:], [(shor[:4], 3), (shor[4:], 1)])]
+    for flat, parts in cases:
+        a, b = qs.Circuit(flat), qs.Circuit.repeated(parts)
+        assert a.n_gates == b.n_gates == len(flat)
+        for i in range(a.n_gates):
+            x, y = a.gates[i], b.gates[i]
+            assert (x.kind, x.k, list(x.targets), x.ctrl_mask) == (y.kind, y.k, list(y.targets), y.ctrl_mask)
+            if x.kind == qs.QS_GATE_PERM:
+                k = 1 << x.k
+                assert np.array_equal(a.perm[x.offset:x.offset + k], b.perm[y.offset:y.offset + k])
+            else:
+                size = {qs.QS_GATE_U1: 8, qs.QS_GATE_UK: 2 * (1 << x.k) ** 2, qs.QS_GATE_DIAG: 2 * (1 << x.k)}[x.kind]
+                assert np.array_equal(a.data[x.offset:x.offset + size], b.data[y.offset:y.offset + size])
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
