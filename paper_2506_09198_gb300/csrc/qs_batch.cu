@@ -326,6 +326,7 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
     gates = xp.run(gates);
     MatFuser mf;  // state's blocks are copied out
     gates = mf.run(gates);
+    const int max_high = std::max(2, std::min(kTileMaxHigh, fuse_width_for(s)));
     bstates[i].psi = s->psi;
     bstates[i].block0 = (uint32_t)blocks.size();
     bstates[i].tau0 = 0;
@@ -338,8 +339,13 @@ qs_status compile_batch(qs_state* states, const qs_circuit* const* circuits, int
         continue;
       }
       Geom geom;
-      const std::vector<size_t> members =
-          choose_block(gates, taken, next, s->n, TP::kTileLog, kTileMaxHigh, min_chunk, lim, 512, &geom);
+      // The fusion width qs_autotune chose for this qubit count (4 untuned):
+      // wider blocks take more strided qubits, each halving the contiguous
+      // chunk a bulk copy moves.
+      std::vector<size_t> members =
+          choose_block(gates, taken, next, s->n, TP::kTileLog, max_high, min_chunk, lim, 512, &geom);
+      if (members.empty() && max_high < kTileMaxHigh)  // a gate wider than the tuned block
+        members = choose_block(gates, taken, next, s->n, TP::kTileLog, kTileMaxHigh, min_chunk, lim, 512, &geom);
       if (members.empty()) return fail(QS_ERR_UNSUPPORTED, "batch state %d: gate %zu fits no tile", i, next);
       PlanBuilder<typename TP::M> pb(&bo, geom, lim);
       size_t emitted = 0;

@@ -178,15 +178,16 @@ def test_x_conjugation_rewrite(mode, max_fuse):
 def test_grover_iteration_takes_few_passes(mode):
     """With the oracle's and the diffusion's X gates moved through their
     multi-controlled Z, a Grover iteration on 16 qubits is two phases on a
-    bit pattern and two H layers: a handful of fused passes, not one per X
-    layer."""
+    bit pattern and two H layers; each H layer spans two tiles (11 qubits
+    complex128, 12 complex64, 4 of them strided), so at most 4 fused passes
+    per iteration."""
     n, marked, r = 16, 12345, 20
     st = new_state(n, mode)
     st.run(W.grover(n, marked, r), max_fuse=4)
     passes = qs().qs_last_run_stats(st.h)["fused_launches"]
     got = st.read()
     st.close()
-    assert passes <= 3 * r + 4, f"{passes} fused passes for {r} Grover iterations"
+    assert passes <= 4 * r + 4, f"{passes} fused passes for {r} Grover iterations"
     assert_state(got, O.run_circuit(O.basis_state(n), W.grover(n, marked, r)), mode, "Grover 16q")
 
 
