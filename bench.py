@@ -525,7 +525,9 @@ def measure_batch(qs, torch, count, nmin, nmax, dtype_name="c128", seed=2512, ch
     if checks:
         g_err, g_fid, s_err, n_shor, n_grover = 0.0, 1.0, 0.0, 0, 0
         for i, (st, m) in enumerate(zip(states, meta)):
-            if m[0] == "grover" and i % 8 == 0:  # every 4th Grover state
+            if m[0] == "grover":
+                if i % 8:  # every 4th Grover state
+                    continue
                 n_grover += 1
                 _, n, marked = m
                 got = st.read().astype(np.complex128)

@@ -89,6 +89,25 @@ qs_status qs_create(int n, qs_dtype dtype, qs_state* out);
  * stream may be NULL (legacy default stream). */
 qs_status qs_wrap(int n, qs_dtype dtype, void* device_ptr, void* stream, qs_state* out);
 
+/* A state larger than HBM allows: the top g qubits (1 <= g <= 6) select one
+ * of 2^g segments of 2^(n-g) amplitudes; segments 0 .. hbm_segments - 1 are
+ * allocated in device memory (cudaMalloc), the others in pinned host memory
+ * that the GPU reads and writes directly (cudaHostAlloc, mapped; over
+ * NVLink-C2C on Grace).  The paper places a state that outgrows one memory
+ * across two (Sec. II-B, NUMA V1/V2); this is that placement for HBM and host
+ * memory.  n - g >= 10 (a gate's targets and controls must fit the local
+ * qubits with room to spare).  The handle takes every call that takes a state
+ * except qs_wrap, qs_device_ptr, qs_autotune and the batched calls
+ * (QS_ERR_UNSUPPORTED).  A gate on local qubits runs on each segment; a
+ * control on a global qubit selects segments; a diagonal gate's global
+ * targets are fixed per segment; a gate that needs a global qubit as a target
+ * first swaps it with a local qubit (half of every segment pair is
+ * exchanged), and an internal qubit map keeps the logical order, which
+ * qs_copy_out, qs_gather and qs_probs restore first.  Segments in host memory
+ * run on the per-gate kernels only; segments in device memory also run fused
+ * blocks.  State |0...0>.  QS_ERR_OOM if an allocation fails. */
+qs_status qs_create_split(int n, qs_dtype dtype, int g, int hbm_segments, qs_state* out);
+
 /* Release the handle (and its memory if it owns it).  NULL is accepted. */
 qs_status qs_destroy(qs_state s);
 

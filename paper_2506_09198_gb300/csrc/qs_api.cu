@@ -37,7 +37,7 @@ qs_status cuda_fail(cudaError_t e, const char* what) {
 constexpr int kErrSlots = 8192;
 __device__ uint32_t g_err_words[kErrSlots];
 
-namespace {
+namespace slots {
 std::mutex g_slot_mu;
 std::vector<int> g_free_slots;
 bool g_slots_init = false;
@@ -61,6 +61,10 @@ void release_err_slot(int slot) {
   g_free_slots.push_back(slot);
 }
 
+}  // namespace slots
+using namespace slots;
+
+namespace {
 uint32_t* err_words(int device) {
   static std::mutex mu;
   static void* addr[64] = {nullptr};
@@ -137,6 +141,33 @@ qs_status ensure_host_scratch(qs_state s, size_t bytes) {
   QS_CUDA(cudaMallocHost(&s->host_scratch, want));
   s->host_scratch_bytes = want;
   return QS_OK;
+}
+
+qs_state new_sub_state(int n, qs_dtype dtype, void* psi) {
+  qs_state s = new (std::nothrow) qs_state_s();
+  if (!s) return nullptr;
+  s->n = n;
+  s->dtype = dtype;
+  s->psi = psi;
+  s->owns = false;
+  if (cudaGetDevice(&s->device) != cudaSuccess) s->device = 0;
+  s->err_slot = acquire_err_slot();
+  return s;
+}
+
+void free_sub_state(qs_state s) {
+  if (!s) return;
+  if (s->err_slot > 0) {
+    uint32_t* w = error_word(s);
+    if (w) {
+      cudaMemsetAsync(w, 0, sizeof(uint32_t), s->stream);
+      cudaStreamSynchronize(s->stream);
+    }
+    release_err_slot(s->err_slot);
+  }
+  if (s->scratch) cudaFree(s->scratch);
+  if (s->host_scratch) cudaFreeHost(s->host_scratch);
+  delete s;
 }
 
 void release_plan_cache(qs_state s);  // qs_circuit.cu
@@ -276,6 +307,7 @@ qs_status qs_wrap(int n, qs_dtype dtype, void* device_ptr, void* stream, qs_stat
 
 qs_status qs_destroy(qs_state s) {
   if (!s) return QS_OK;
+  if (s->split) split_destroy(s);
   cudaStreamSynchronize(s->stream);
   release_plan_cache(s);
   if (s->err_slot > 0) {
@@ -298,6 +330,7 @@ qs_status qs_set_stream(qs_state s, void* cuda_stream) {
   qs_status st = check_state(s);
   if (st != QS_OK) return st;
   s->stream = (cudaStream_t)cuda_stream;
+  if (s->split) split_set_stream(s, s->stream);
   return QS_OK;
 }
 
@@ -306,6 +339,7 @@ qs_status qs_set_math(qs_state s, qs_math math) {
   if (st != QS_OK) return st;
   if (math != QS_MATH_DF && math != QS_MATH_FP64) return fail(QS_ERR_ARG, "unknown math mode %d", (int)math);
   s->math = math;
+  if (s->split) split_set_math(s, math);
   return QS_OK;
 }
 
@@ -321,6 +355,7 @@ qs_status qs_device_ptr(qs_state s, void** p) {
   qs_status st = check_state(s);
   if (st != QS_OK) return st;
   if (!p) return fail(QS_ERR_ARG, "output pointer is NULL");
+  if (s->split) return fail(QS_ERR_UNSUPPORTED, "a split state has no single device pointer");
   *p = s->psi;
   return QS_OK;
 }
@@ -329,6 +364,7 @@ qs_status qs_init_basis(qs_state s, uint64_t idx) {
   qs_status st = check_state(s);
   if (st != QS_OK) return st;
   if (idx >= (1ull << s->n)) return fail(QS_ERR_ARG, "basis index out of range");
+  if (s->split) return split_init_basis(s, idx);
   return launch_init_basis(s, idx);
 }
 
@@ -336,6 +372,7 @@ qs_status qs_copy_in(qs_state s, const void* host) {
   qs_status st = check_state(s);
   if (st != QS_OK) return st;
   if (!host) return fail(QS_ERR_ARG, "host is NULL");
+  if (s->split) return split_copy_in(s, host);
   QS_CUDA(cudaMemcpyAsync(s->psi, host, amp_bytes(s->dtype) << s->n, cudaMemcpyHostToDevice, s->stream));
   return QS_OK;
 }
@@ -344,6 +381,7 @@ qs_status qs_copy_out(qs_state s, void* host) {
   qs_status st = check_state(s);
   if (st != QS_OK) return st;
   if (!host) return fail(QS_ERR_ARG, "host is NULL");
+  if (s->split) return split_copy_out(s, host, true);
   QS_CUDA(cudaMemcpyAsync(host, s->psi, amp_bytes(s->dtype) << s->n, cudaMemcpyDeviceToHost, s->stream));
   QS_CUDA(cudaStreamSynchronize(s->stream));
   return device_error_check(s);
@@ -353,6 +391,7 @@ qs_status qs_copy_out_async(qs_state s, void* host) {
   qs_status st = check_state(s);
   if (st != QS_OK) return st;
   if (!host) return fail(QS_ERR_ARG, "host is NULL");
+  if (s->split) return split_copy_out(s, host, false);
   QS_CUDA(cudaMemcpyAsync(host, s->psi, amp_bytes(s->dtype) << s->n, cudaMemcpyDeviceToHost, s->stream));
   return QS_OK;
 }
@@ -363,6 +402,7 @@ qs_status qs_gather(qs_state s, const uint64_t* idx, int64_t count, void* host_o
   if (count < 0 || (count > 0 && (!idx || !host_out))) return fail(QS_ERR_ARG, "bad gather arguments");
   for (int64_t j = 0; j < count; ++j)
     if (idx[j] >= (1ull << s->n)) return fail(QS_ERR_ARG, "gather index %lld out of range", (long long)j);
+  if (s->split) return split_gather(s, idx, count, host_out);
   return run_gather(s, idx, count, host_out);
 }
 
@@ -372,6 +412,7 @@ qs_status qs_apply_1q(qs_state s, int target, const double U[8]) {
   uint64_t cm = 0;
   if ((st = check_qubits(s, nullptr, 0, &target, 1, &cm)) != QS_OK) return st;
   if ((st = check_finite(U, 8, "U")) != QS_OK) return st;
+  if (s->split) return split_gate(s, QS_GATE_U1, &target, 1, 0, U, 8, nullptr);
   return dispatch_u1(s, target, 0, U);
 }
 
@@ -382,6 +423,7 @@ qs_status qs_apply_2q(qs_state s, int t0, int t1, const double U[32]) {
   uint64_t cm = 0;
   if ((st = check_qubits(s, nullptr, 0, tg, 2, &cm)) != QS_OK) return st;
   if ((st = check_finite(U, 32, "U")) != QS_OK) return st;
+  if (s->split) return split_gate(s, QS_GATE_UK, tg, 2, 0, U, 32, nullptr);
   return dispatch_uk(s, tg, 2, 0, U);
 }
 
@@ -391,6 +433,7 @@ qs_status qs_apply_ctrl(qs_state s, const int* ctrls, int nctrl, int target, con
   uint64_t cm = 0;
   if ((st = check_qubits(s, ctrls, nctrl, &target, 1, &cm)) != QS_OK) return st;
   if ((st = check_finite(U, 8, "U")) != QS_OK) return st;
+  if (s->split) return split_gate(s, QS_GATE_U1, &target, 1, cm, U, 8, nullptr);
   return dispatch_u1(s, target, cm, U);
 }
 
@@ -401,6 +444,7 @@ qs_status qs_apply_diag(qs_state s, const int* targets, int k, const double* d) 
   uint64_t cm = 0;
   if ((st = check_qubits(s, nullptr, 0, targets, k, &cm)) != QS_OK) return st;
   if ((st = check_finite(d, (size_t)2 << k, "d")) != QS_OK) return st;
+  if (s->split) return split_gate(s, QS_GATE_DIAG, targets, k, 0, d, (size_t)2 << k, nullptr);
   return dispatch_diag(s, targets, k, 0, d);
 }
 
@@ -416,6 +460,7 @@ qs_status qs_apply_perm(qs_state s, const int* ctrls, int nctrl, const int* targ
     if (perm[v] >= (1u << k) || seen[perm[v]]) return fail(QS_ERR_ARG, "perm is not a bijection of 0..2^k-1");
     seen[perm[v]] = 1;
   }
+  if (s->split) return split_gate(s, QS_GATE_PERM, targets, k, cm, nullptr, 0, perm);
   return dispatch_perm(s, targets, k, cm, perm);
 }
 
@@ -423,6 +468,7 @@ qs_status qs_norm(qs_state s, double* out) {
   qs_status st = check_state(s);
   if (st != QS_OK) return st;
   if (!out) return fail(QS_ERR_ARG, "out is NULL");
+  if (s->split) return split_norm(s, out);
   return run_norm(s, out);
 }
 
@@ -433,6 +479,7 @@ qs_status qs_probs(qs_state s, const int* qubits, int k, double* out) {
   if (!out) return fail(QS_ERR_ARG, "out is NULL");
   uint64_t cm = 0;
   if ((st = check_qubits(s, nullptr, 0, qubits, k, &cm)) != QS_OK) return st;
+  if (s->split) return split_probs(s, qubits, k, out);
   return run_probs(s, qubits, k, out);
 }
 
@@ -455,6 +502,7 @@ qs_status qs_sync(qs_state s, double timeout_s) {
     if (el > timeout_s) return fail(QS_ERR_TIMEOUT, "stream not drained after %.3f s", timeout_s);
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
+  if (s->split) return split_check(s);
   return device_error_check(s);
 }
 

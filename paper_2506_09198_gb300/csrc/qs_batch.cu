@@ -664,6 +664,7 @@ qs_status batch_check(qs_state* states, const qs_circuit* const* circuits, int c
   const qs_state s0 = states[0];
   for (int i = 0; i < count; ++i) {
     if (!states[i] || !circuits[i]) return fail(QS_ERR_ARG, "batch entry %d is NULL", i);
+    if (states[i]->split) return fail(QS_ERR_UNSUPPORTED, "batch entry %d is a split state", i);
     if (states[i]->dtype != s0->dtype || states[i]->math != s0->math)
       return fail(QS_ERR_ARG, "batch entry %d: every state must have the dtype and math mode of the first", i);
     if (states[i]->device != s0->device) return fail(QS_ERR_ARG, "batch entry %d is on another device", i);

@@ -135,6 +135,7 @@ qs_status qs_fuse_run(qs_state s, const qs_circuit* c, const qs_run_opts* opts) 
   s->run_fused_launches = 0;
   s->run_gate_launches = 0;
   if (c->n_gates == 0) return QS_OK;
+  if (s->split) return split_run(s, c, max_fuse);
   if (max_fuse != 1) return run_fused(s, c, max_fuse == 0 ? tuned_max_fuse(s) : max_fuse);
   s->run_gate_launches = c->n_gates;
   return qs_fuse_run_gatewise(s, c);
@@ -151,6 +152,7 @@ qs_status qs_last_run_stats(qs_state s, qs_run_stats* out) {
 
 qs_status qs_autotune(qs_state s, const qs_circuit* c, int* best_max_fuse, double* best_ms) {
   if (!s) return fail(QS_ERR_ARG, "state handle is NULL");
+  if (s->split) return fail(QS_ERR_UNSUPPORTED, "autotuning takes a state in one allocation");
   if (!c || c->n_gates < 0 || (c->n_gates > 0 && !c->gates)) return fail(QS_ERR_ARG, "bad circuit");
   for (int64_t i = 0; i < c->n_gates; ++i) {
     qs_status st = check_gate(s, c, i);

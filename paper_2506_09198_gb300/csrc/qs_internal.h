@@ -26,6 +26,9 @@ struct qs_state_s {
   // Launches of the last qs_fuse_run on this state (qs_last_run_stats).
   int64_t run_fused_launches = 0;
   int64_t run_gate_launches = 0;
+  // Split state (qs_create_split): segments, placement and qubit map
+  // (qs_split.cu); nullptr for a state in one allocation.
+  void* split = nullptr;
 };
 
 namespace qs {
@@ -99,6 +102,29 @@ qs_status dispatch_perm(qs_state s, const int* targets, int k, uint64_t ctrl_mas
 void turn_cos_sin(uint32_t m, double* c, double* s);
 qs_status ensure_phase_tables(int device);
 const void* phase_table(int device, int format);
+
+// Internal handles: a state record over memory the caller manages (psi may
+// be nullptr), with its own error word; free_sub_state releases the record
+// and its scratch buffers, never psi.
+qs_state new_sub_state(int n, qs_dtype dtype, void* psi);
+void free_sub_state(qs_state s);
+
+// Split states (qs_split.cu).
+qs_status split_run(qs_state s, const qs_circuit* c, int max_fuse);
+// One gate given through the single-gate calls (arguments validated).
+qs_status split_gate(qs_state s, int kind, const int* targets, int k, uint64_t ctrl_mask, const double* data,
+                     size_t ndata, const uint32_t* perm);
+qs_status split_init_basis(qs_state s, uint64_t idx);
+qs_status split_copy_in(qs_state s, const void* host);
+qs_status split_copy_out(qs_state s, void* host, bool sync);
+qs_status split_gather(qs_state s, const uint64_t* idx, int64_t count, void* host_out);
+qs_status split_norm(qs_state s, double* out);
+qs_status split_probs(qs_state s, const int* qubits, int k, double* out);
+qs_status split_check(qs_state s);
+void split_set_stream(qs_state s, cudaStream_t stream);
+void split_set_math(qs_state s, qs_math math);
+void split_destroy(qs_state s);
+qs_status qs_fuse_run_gatewise(qs_state s, const qs_circuit* c);
 
 qs_status ensure_scratch(qs_state s, size_t bytes);
 qs_status ensure_host_scratch(qs_state s, size_t bytes);

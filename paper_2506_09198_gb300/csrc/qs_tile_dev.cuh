@@ -18,7 +18,13 @@ namespace qs {
 #ifndef QS_TILE_MIN_CTAS
 #define QS_TILE_MIN_CTAS 2
 #endif
-constexpr int kTileConsumers = 256;
+// Consumer threads per CTA (a power of two); a tile is kTileConsumers x 2^RB
+// amplitudes, RB the policy's register bits.
+#ifndef QS_TILE_CONSUMERS_LOG
+#define QS_TILE_CONSUMERS_LOG 8
+#endif
+constexpr int kTileConsumersLog = QS_TILE_CONSUMERS_LOG;
+constexpr int kTileConsumers = 1 << kTileConsumersLog;
 constexpr int kTileThreads = kTileConsumers + 32;
 constexpr int kStages = QS_TILE_STAGES;
 constexpr int kTileMinCtas = QS_TILE_MIN_CTAS;
@@ -112,7 +118,7 @@ struct TileF32 {
   static constexpr bool kStagePlan = true;
   using Glob = float2;
   using Sm = float2;
-  static constexpr int kTileLog = 12;  // 4096 amplitudes, 32 KB
+  static constexpr int kTileLog = kTileConsumersLog + 4;  // 4096 amplitudes, 32 KB (256 consumers)
   static constexpr int kRegBits = 4;  // 16 amplitudes per thread
   static constexpr int kBankBits = 4;  // 16 amplitudes per 128-byte shared-memory row
   static __device__ __forceinline__ Sm to_sm(Glob g) { return g; }
@@ -191,7 +197,7 @@ struct TileF64 {
   static constexpr bool kStagePlan = true;
   using Glob = double2;
   using Sm = double2;
-  static constexpr int kTileLog = 11;  // 2048 amplitudes, 32 KB
+  static constexpr int kTileLog = kTileConsumersLog + 3;  // 2048 amplitudes, 32 KB (256 consumers)
   static constexpr int kRegBits = 3;  // 8 amplitudes per thread
   static constexpr int kBankBits = 3;  // 8 amplitudes per 128-byte shared-memory row
   static __device__ __forceinline__ Sm to_sm(Glob g) { return g; }
@@ -239,7 +245,7 @@ struct TileDF {
   static constexpr bool kHoistCoefs = false;
   using Glob = double2;
   using Sm = float4;
-  static constexpr int kTileLog = 11;
+  static constexpr int kTileLog = kTileConsumersLog + 3;
   static constexpr int kRegBits = 3;  // 8 amplitudes per thread
   static constexpr int kBankBits = 3;  // 8 amplitudes per 128-byte shared-memory row
   static __device__ __forceinline__ Sm to_sm(Glob g) {

@@ -92,6 +92,7 @@ _SIGS = {
     "qs_batch_destroy": [_P],
     "qs_set_wait_limit": [ctypes.c_double],
     "qs_last_run_stats": [_P, ctypes.POINTER(qs_run_stats)],
+    "qs_create_split": [_I, _I, _I, _I, ctypes.POINTER(_P)],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -136,6 +137,14 @@ def qs_version() -> str:
 def qs_create(n: int, dtype: int):
     h = _P()
     _check(_lib.qs_create(n, dtype, ctypes.byref(h)))
+    return h
+
+
+def qs_create_split(n: int, dtype: int, g: int, hbm_segments: int):
+    """A state of n qubits in 2^g segments, the first hbm_segments in device
+    memory and the rest in pinned host memory."""
+    h = _P()
+    _check(_lib.qs_create_split(n, dtype, g, hbm_segments, ctypes.byref(h)))
     return h
 
 
@@ -424,6 +433,11 @@ class State:
     @property
     def np_dtype(self):
         return np.complex64 if self.dtype == QS_C64 else np.complex128
+
+    @classmethod
+    def split(cls, n: int, dtype: int = QS_C128, g: int = 1, hbm_segments: int = 1, math: int = QS_MATH_DF):
+        """A state split over device and host memory (qs_create_split)."""
+        return cls(n, dtype, math, handle=qs_create_split(n, dtype, g, hbm_segments))
 
     def close(self):
         if self.h is not None:
