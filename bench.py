@@ -19,7 +19,9 @@ After the timed region the line gains (bounded in time):
   - 4096 batched Grover / Shor-like states of 10..20 qubits (one compiled,
     graph-captured batch), with closed-form checks;
   - the serving loop on a stream of requests of 12..30 qubits (admission
-    closed after a stated time), complex64 and complex128.
+    closed after a stated time), complex64 and complex128;
+  - a 32-qubit complex128 state split over HBM and host memory: a gate on a
+    local and on the global qubit.
 A compact "summary" object closes the line.
 
 Prints one JSON line.  --impl reference times the CPU oracle on a bounded
@@ -73,7 +75,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip every measurement taken after the timed region")
-    ap.add_argument("--extras", default="kinds,variants,circuits,batch,serve",
+    ap.add_argument("--extras", default="kinds,variants,circuits,batch,serve,split",
                     help="comma list of the extras to take after the timed region")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "circuits", "batch", "serve"],
                     help="sweep: the default gate sweep; the others print one line each for the fused "
@@ -154,6 +156,42 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+class BusySampler:
+    """GPU utilisation (nvidia-smi utilization.gpu, 100 ms samples) over a
+    region: the fraction of time a kernel was running."""
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.vals = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=utilization.gpu", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            try:
+                self.vals.append(float(line.strip()))
+            except ValueError:
+                pass
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        return {"mean_pct": statistics.mean(self.vals), "samples": len(self.vals)} if self.vals else None
 
 
 # ---------------------------------------------------------------------------
@@ -593,9 +631,12 @@ def measure_serving(qs, torch, requests, nmin, nmax, admit_s=0.0, seed=2513, fra
         srv = S.Server(dt, hbm_budget_bytes=budget)
         for r in S.make_requests(requests, seed=seed, n_min=nmin, n_max=nmax, rate=0.0):
             srv.submit(r)
+        busy = BusySampler(torch.cuda.current_device())
+        busy.start()
         t0 = time.perf_counter()
         done = srv.run(admit_until=admit_s or None)
         cap = S.summarize(done, time.perf_counter() - t0)
+        cap["gpu_busy"] = busy.stop()
         cap["dropped"] = len(srv.dropped)
         res["capacity"] = cap
         results[dname] = {r.rid: r for r in done}
@@ -650,6 +691,33 @@ def served_fidelity_sample(qs, torch, seed, nmin, nmax, count=24, n_cap=24):
         qs.qs_destroy(ha)
         qs.qs_destroy(hb)
     return {"min": worst, "requests": len(picked), "qubits_at_most": n_cap}
+
+
+def measure_split(qs, torch, n=32, seed=2530):
+    """A complex128 state of n qubits in two segments, one in HBM and one in
+    pinned host memory (NVLink-C2C): device time of a dense gate on a local
+    qubit and on the global qubit (which first swaps it in), algorithmic GB/s,
+    and the norm after them (FP64 reduction over both segments)."""
+    t0 = time.perf_counter()
+    st = qs.State.split(n, qs.QS_C128, 1, 1)
+    alloc_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    qs.qs_set_stream(st.h, stream.cuda_stream)
+    U = W.haar_unitary(2, W.rng_for(seed))
+    qs.qs_apply_1q(st.h, 0, W.mat_h())  # a state with every amplitude in both segments
+    res = {"n_qubits": n, "segments": "2 (1 in HBM, 1 in pinned host memory)", "alloc_s": alloc_s}
+    for label, t in (("local_gate_q20", 20), ("global_gate_swap_in", n - 1), ("gate_on_swapped_qubit", n - 1)):
+        a, b = _events(torch)
+        torch.cuda.synchronize()
+        a.record(stream)
+        qs.qs_apply_1q(st.h, t, U)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        res[label] = {"ms": ms, "gbs": gate_bytes(n, 16) / (ms * 1e-3) / 1e9}
+    res["norm_err"] = abs(st.norm() - 1.0)
+    st.close()
+    return res
 
 
 def run_extra_workload(args):
@@ -744,6 +812,10 @@ def summarize_extras(ex, peak):
                                "p50_0.7": r(p7.get("p50_ms"), 1), "p99_0.7": r(p7.get("p99_ms"), 1),
                                "err": sv[d].get("max_err_vs_closed_form")}
         s["serve_fid_c64"] = sv.get("c64_vs_c128_state_fidelity", {}).get("min")
+        s["serve_gpu_busy_pct"] = {d: (sv[d]["capacity"].get("gpu_busy") or {}).get("mean_pct") for d in ("c128", "c64")}
+    sp = ex.get("split_32q_c128")
+    if sp:
+        s["split_32q_gbs"] = {"local": r(sp["local_gate_q20"]["gbs"]), "global": r(sp["global_gate_swap_in"]["gbs"])}
     return s
 
 
@@ -902,6 +974,8 @@ def run_ours(args):
             extras["batched_c64"] = measure_batch(qs, torch, 4096, 10, 20, "c64", launches=1)
         if "serve" in want:
             extras["serving"] = measure_serving(qs, torch, 2000, 12, 30, admit_s=12.0, fracs=(0.7,))
+        if "split" in want:
+            extras["split_32q_c128"] = measure_split(qs, torch)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
