@@ -69,7 +69,8 @@ typedef struct qs_state_s* qs_state;
 
 enum {
   QS_MAX_QUBITS = 40,     /* index arithmetic limit; memory limits come first */
-  QS_MAX_TARGETS = 8      /* largest target set of a diagonal/permutation gate */
+  QS_MAX_TARGETS = 8,     /* largest target set of a diagonal/permutation gate */
+  QS_MAX_DENSE = 5        /* largest target set of a general (dense) matrix gate */
 };
 
 /* ---- state lifetime -------------------------------------------------- */
@@ -113,6 +114,16 @@ qs_status qs_destroy(qs_state s);
 
 qs_status qs_set_stream(qs_state s, void* cuda_stream);
 qs_status qs_set_math(qs_state s, qs_math math);
+/* Engine for complex64 dense gates on 4 and 5 targets (qs_apply_dense,
+ * QS_GATE_UK); 3 targets always run on the FP32 CUDA cores, which keep up
+ * with HBM there.
+ * 1 (default): the tensor cores.  Each group of 2^k amplitudes is a row of a
+ *   GEMM with the gate's real 2^(k+1) x 2^(k+1) form; operands are split into
+ *   TF32 head and remainder and three products are summed in FP32, so the
+ *   error stays at FP32's level (about 1e-7 relative to the gate's row norms).
+ * 0: one FP32 FMA chain per output on the CUDA cores.
+ * complex128 states ignore it: they use FP64 FMA chains on the CUDA cores. */
+qs_status qs_set_tensor_cores(qs_state s, int enable);
 qs_status qs_num_qubits(qs_state s, int* n);
 qs_status qs_device_ptr(qs_state s, void** device_ptr);
 
@@ -155,6 +166,17 @@ qs_status qs_apply_2q(qs_state s, int t0, int t1, const double U[32]);
  * CNOT is ctrl = {c}, U = X. */
 qs_status qs_apply_ctrl(qs_state s, const int* ctrls, int nctrl, int target, const double U[8]);
 
+/* General gate: the 2^k x 2^k matrix U (row-major, (re, im) pairs) on k
+ * targets (1 <= k <= QS_MAX_DENSE) where all nctrl controls are 1.  Sub-
+ * register value s = sum_j bit(i, targets[j]) 2^j indexes rows and columns;
+ * each group of 2^k amplitudes sharing the other bits is multiplied by U
+ * (Sec. II-B: a k-qubit gate is a 2^k x 2^k unitary on its index bits).
+ * Diagonal and permutation matrices run as qs_apply_diag / qs_apply_perm;
+ * dense matrices on 4 or 5 targets run on the tensor cores for complex64
+ * states (qs_set_tensor_cores), on 3 targets on FP32 CUDA cores; complex128
+ * states use FP64 CUDA cores. */
+qs_status qs_apply_dense(qs_state s, const int* ctrls, int nctrl, const int* targets, int k, const double* U);
+
 /* Diagonal gate on k targets (1 <= k <= QS_MAX_TARGETS):
  * psi_i <- d[s(i)] psi_i with s(i) = sum_j bit(i, targets[j]) 2^j; d holds
  * 2^k complex entries (re, im).  Controlled phase shifts (Sec. III-B) and
@@ -172,9 +194,9 @@ qs_status qs_apply_perm(qs_state s, const int* ctrls, int nctrl, const int* targ
 
 typedef enum {
   QS_GATE_U1 = 0,    /* 2x2 matrix on targets[0] */
-  QS_GATE_UK = 1,    /* 2^k x 2^k matrix: any for k <= 2; for 3 <= k <= 8 only
-                        diagonal or permutation matrices (QS_ERR_UNSUPPORTED
-                        otherwise) */
+  QS_GATE_UK = 1,    /* 2^k x 2^k matrix: any for k <= QS_MAX_DENSE (5; see
+                        qs_apply_dense); for 6 <= k <= 8 only diagonal or
+                        permutation matrices (QS_ERR_UNSUPPORTED otherwise) */
   QS_GATE_DIAG = 2,  /* 2^k diagonal entries */
   QS_GATE_PERM = 3   /* uint32 table of 2^k entries */
 } qs_gate_kind;

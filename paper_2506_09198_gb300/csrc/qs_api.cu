@@ -343,6 +343,15 @@ qs_status qs_set_math(qs_state s, qs_math math) {
   return QS_OK;
 }
 
+qs_status qs_set_tensor_cores(qs_state s, int enable) {
+  qs_status st = check_state(s);
+  if (st != QS_OK) return st;
+  if (enable != 0 && enable != 1) return fail(QS_ERR_ARG, "enable must be 0 or 1");
+  s->tensor_cores = enable;
+  if (s->split) split_set_tensor_cores(s, enable);
+  return QS_OK;
+}
+
 qs_status qs_num_qubits(qs_state s, int* n) {
   qs_status st = check_state(s);
   if (st != QS_OK) return st;
@@ -435,6 +444,19 @@ qs_status qs_apply_ctrl(qs_state s, const int* ctrls, int nctrl, int target, con
   if ((st = check_finite(U, 8, "U")) != QS_OK) return st;
   if (s->split) return split_gate(s, QS_GATE_U1, &target, 1, cm, U, 8, nullptr);
   return dispatch_u1(s, target, cm, U);
+}
+
+qs_status qs_apply_dense(qs_state s, const int* ctrls, int nctrl, const int* targets, int k, const double* U) {
+  qs_status st = check_state(s);
+  if (st != QS_OK) return st;
+  if (k < 1 || k > QS_MAX_DENSE) return fail(QS_ERR_ARG, "k = %d outside [1, %d]", k, (int)QS_MAX_DENSE);
+  uint64_t cm = 0;
+  if ((st = check_qubits(s, ctrls, nctrl, targets, k, &cm)) != QS_OK) return st;
+  const size_t nd = (size_t)2 << (2 * k);
+  if ((st = check_finite(U, nd, "U")) != QS_OK) return st;
+  if (s->split) return split_gate(s, k == 1 ? QS_GATE_U1 : QS_GATE_UK, targets, k, cm, U, nd, nullptr);
+  if (k == 1) return dispatch_u1(s, targets[0], cm, U);
+  return dispatch_uk(s, targets, k, cm, U);
 }
 
 qs_status qs_apply_diag(qs_state s, const int* targets, int k, const double* d) {

@@ -51,7 +51,7 @@ qs_status check_gate(const qs_state s, const qs_circuit* c, int64_t gi) {
       break;
     case QS_GATE_UK: {
       if (!c->data) return fail(QS_ERR_ARG, "circuit has no data pool");
-      if (g.k <= 2) break;
+      if (g.k <= 5) break;
       // Larger matrices are accepted when they are diagonal or permutations.
       const int dim = 1 << g.k;
       const double* M = c->data + g.offset;
@@ -70,7 +70,7 @@ qs_status check_gate(const qs_state s, const qs_circuit* c, int64_t gi) {
         if (ones != 1) permlike = false;
       }
       if (!diag && !permlike)
-        return fail(QS_ERR_UNSUPPORTED, "gate %lld: dense matrices on %d targets are not supported (at most 2)",
+        return fail(QS_ERR_UNSUPPORTED, "gate %lld: dense matrices on %d targets are not supported (at most 5)",
                     (long long)gi, g.k);
       break;
     }

@@ -656,7 +656,8 @@ qs_status dispatch_uk(qs_state s, const int* targets, int k, uint64_t ctrl_mask,
   }
   if (k == 1) return launch_dense1(s, targets[0], ctrl_mask, M);
   if (k == 2) return launch_dense2(s, targets[0], targets[1], ctrl_mask, M);
-  return fail(QS_ERR_UNSUPPORTED, "dense gates on %d targets go through qs_fuse_run", k);
+  if (k <= 5) return launch_dense_k(s, targets, k, ctrl_mask, M);
+  return fail(QS_ERR_UNSUPPORTED, "dense gates on %d targets (at most 5)", k);
 }
 
 }  // namespace qs

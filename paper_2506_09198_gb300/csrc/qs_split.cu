@@ -507,6 +507,10 @@ void split_set_math(qs_state s, qs_math math) {
   for (qs_state seg : info(s)->seg) seg->math = math;
 }
 
+void split_set_tensor_cores(qs_state s, int enable) {
+  for (qs_state seg : info(s)->seg) seg->tensor_cores = enable;
+}
+
 void split_destroy(qs_state s) {
   SplitInfo* si = info(s);
   cudaStreamSynchronize(s->stream);

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libqs.so")
 QS_OK, QS_ERR_ARG, QS_ERR_OOM, QS_ERR_CUDA, QS_ERR_TIMEOUT, QS_ERR_UNSUPPORTED, QS_ERR_DEVICE = range(7)
 QS_C64, QS_C128 = 0, 1
 QS_MATH_DF, QS_MATH_FP64 = 0, 1
-QS_MAX_QUBITS, QS_MAX_TARGETS = 40, 8
+QS_MAX_QUBITS, QS_MAX_TARGETS, QS_MAX_DENSE = 40, 8, 5
 QS_GATE_U1, QS_GATE_UK, QS_GATE_DIAG, QS_GATE_PERM = 0, 1, 2, 3
 STATUS_NAMES = {0: "QS_OK", 1: "QS_ERR_ARG", 2: "QS_ERR_OOM", 3: "QS_ERR_CUDA", 4: "QS_ERR_TIMEOUT",
                 5: "QS_ERR_UNSUPPORTED", 6: "QS_ERR_DEVICE"}
@@ -79,6 +79,8 @@ _SIGS = {
     "qs_apply_2q": [_P, _I, _I, _PD],
     "qs_apply_ctrl": [_P, _PI, _I, _I, _PD],
     "qs_apply_diag": [_P, _PI, _I, _PD],
+    "qs_apply_dense": [_P, _PI, _I, _PI, _I, _PD],
+    "qs_set_tensor_cores": [_P, _I],
     "qs_apply_perm": [_P, _PI, _I, _PI, _I, _PU32],
     "qs_fuse_run": [_P, ctypes.POINTER(qs_circuit), ctypes.POINTER(qs_run_opts)],
     "qs_batch_run": [ctypes.POINTER(_P), ctypes.POINTER(ctypes.POINTER(qs_circuit)), _I, ctypes.POINTER(qs_run_opts)],
@@ -222,6 +224,17 @@ def qs_apply_ctrl(h, ctrls, target: int, U):
     c, pc = _i32(ctrls)
     f, p = _c128_flat(U, 4)
     _check(_lib.qs_apply_ctrl(h, pc, c.size, target, p))
+
+
+def qs_apply_dense(h, ctrls, targets, U):
+    c, pc = _i32(ctrls)
+    t, pt = _i32(targets)
+    f, p = _c128_flat(U, 1 << (2 * t.size))
+    _check(_lib.qs_apply_dense(h, pc, c.size, pt, t.size, p))
+
+
+def qs_set_tensor_cores(h, enable: int):
+    _check(_lib.qs_set_tensor_cores(h, int(enable)))
 
 
 def qs_apply_diag(h, targets, d):
@@ -474,6 +487,8 @@ class State:
                 qs_apply_1q(self.h, g.targets[0], g.data)
         elif g.kind == "uk" and len(g.targets) == 2 and not g.ctrls:
             qs_apply_2q(self.h, g.targets[0], g.targets[1], g.data)
+        elif g.kind == "uk" and len(g.targets) <= QS_MAX_DENSE:
+            qs_apply_dense(self.h, g.ctrls, g.targets, g.data)
         elif g.kind == "diag" and not g.ctrls:
             qs_apply_diag(self.h, g.targets, g.data)
         elif g.kind == "perm":

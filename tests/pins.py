@@ -206,6 +206,35 @@ def pin_tensordot(O, n=12, n_gates=40, seed=200):
         psi = ref
 
 
+def pin_dense_wide(O, seed=250):
+    """Dense gates on 4 and 5 targets (unsorted, 0-2 controls): against the
+    tensordot contraction, and a Kronecker product U_{k-1} (x) ... (x) U_0
+    (target j is bit j of the matrix index, the rightmost factor for j = 0)
+    against the k single-qubit gates applied one by one."""
+    rng = W.rng_for(seed)
+    for k in (4, 5):
+        for n in (k, k + 2, 9):
+            for nc in range(0, min(2, n - k) + 1):
+                qs = W.random_distinct(rng, n, k + nc)
+                tg, cs = qs[:k], qs[k:]
+                psi = W.random_state(n, rng)
+                g = W.gk(tg, W.haar_unitary(1 << k, rng), ctrls=cs)
+                ref = tensordot_apply(psi, g, n)
+                got = O.apply_kq(psi.copy(), tg, g.data, ctrls=cs)
+                assert _maxerr(got, ref) < 1e-14, f"k={k} n={n} t={tg} c={cs}"
+            facs = [W.haar_unitary(2, rng) for _ in range(k)]
+            U = facs[k - 1]
+            for j in range(k - 2, -1, -1):
+                U = np.kron(U, facs[j])
+            tg = W.random_distinct(rng, n, k)
+            psi = W.random_state(n, rng)
+            want = psi.copy()
+            for j in range(k):
+                O.apply_1q(want, tg[j], facs[j])
+            got = O.apply_kq(psi.copy(), tg, U)
+            assert _maxerr(got, want) < 1e-14, f"k={k} n={n}: Kronecker product vs one-qubit gates"
+
+
 def pin_hadamard_uniform(O, ns=range(1, 15)):
     for n in ns:
         psi = O.run_circuit(O.basis_state(n), [W.H(q) for q in range(n)])
@@ -372,6 +401,7 @@ ALL_PINS = [
     pin_textbook_2q,
     pin_bruteforce,
     pin_tensordot,
+    pin_dense_wide,
     pin_hadamard_uniform,
     pin_qft_basis,
     pin_grover,

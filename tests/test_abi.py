@@ -63,6 +63,10 @@ def test_argument_validation_without_gpu(qs):
     for bad in (-1.0, 61.0, float("nan")):
         assert lib.qs_set_wait_limit(bad) == qs.QS_ERR_ARG
     assert lib.qs_set_wait_limit(2.0) == qs.QS_OK
+    t3 = (ctypes.c_int * 3)(0, 1, 2)
+    U8 = (ctypes.c_double * 128)()
+    assert lib.qs_apply_dense(None, None, 0, t3, 3, U8) == qs.QS_ERR_ARG
+    assert lib.qs_set_tensor_cores(None, 1) == qs.QS_ERR_ARG
     for args in ((12, qs.QS_C128, 0, 1), (12, qs.QS_C128, 7, 1), (11, qs.QS_C128, 2, 1), (13, qs.QS_C128, 2, 5),
                  (12, 9, 1, 1)):
         assert lib.qs_create_split(*args, ctypes.byref(h)) == qs.QS_ERR_ARG
