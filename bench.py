@@ -75,11 +75,12 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip every measurement taken after the timed region")
-    ap.add_argument("--extras", default="kinds,variants,circuits,batch,serve,split",
+    ap.add_argument("--extras", default="kinds,variants,dense,circuits,batch,serve,split",
                     help="comma list of the extras to take after the timed region")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "circuits", "batch", "serve"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "circuits", "batch", "serve", "dense"],
                     help="sweep: the default gate sweep; the others print one line each for the fused "
-                         "RQC/QFT circuits, the batched small states and the serving loop")
+                         "RQC/QFT circuits, the batched small states, the serving loop and the dense "
+                         "3..5-target gates (tensor cores vs CUDA cores, complex64, --n qubits)")
     ap.add_argument("--count", type=int, default=4096, help="batch: number of states")
     ap.add_argument("--nmin", type=int, default=10)
     ap.add_argument("--nmax", type=int, default=20)
@@ -720,6 +721,98 @@ def measure_split(qs, torch, n=32, seed=2530):
     return res
 
 
+def tf32_peak():
+    """TF32 dense tensor peak: the measured bf16 burst figure times the nominal
+    TF32 : bf16 ratio (1.1 : 2.25 PFLOP/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 x 1.1/2.25"
+    except Exception:
+        return 1900.0 * 1.1 / 2.25, "fallback bf16 x 1.1/2.25"
+
+
+def measure_dense_k(qs, torch, psi_host, seed=2540):
+    """Dense gates on k = 3, 4, 5 targets (low, high and scattered positions)
+    of a seeded state (the benchmark's 30-qubit one: 8 GiB) in complex64: device time
+    of one launch on the tensor cores (k = 4, 5) and on the FP32 CUDA cores,
+    algorithmic GB/s (one read and one write of the state), useful TFLOP/s
+    (8 2^k real flops per amplitude) and, for the tensor cores, the pipe's
+    TFLOP/s (three TF32 products: 24 2^k flops per amplitude).  Then sampled
+    groups of a k = 5 tensor-core launch against U x in double for each
+    32-amplitude group (sub-register order), as the ratio of the error to the
+    FP32 bound (4 d + 8) 2^-24 sum_c |U_rc||x_c|."""
+    n = int(psi_host.size).bit_length() - 1
+    psi64 = psi_host.astype(np.complex64)
+    dev = torch.from_numpy(psi64.view(np.float32)).cuda()
+    stream = torch.cuda.current_stream()
+    h = qs.qs_wrap(n, qs.QS_C64, dev.data_ptr(), stream.cuda_stream)
+    rng = W.rng_for(seed)
+    peak, peak_src = peaks()
+    tpeak, tpeak_src = tf32_peak()
+    res = {"n_qubits": n, "state": "c64", "launches": {}}
+    best = None
+    for k in (3, 4, 5):
+        U = W.haar_unitary(1 << k, rng)
+        for label, tg in (("low", list(range(k))), ("high", list(range(n - k, n))),
+                          ("scattered", [0, 7, 15, 22, n - 1][:k])):
+            for eng, flag in (("tc", 1), ("cuda_cores", 0)):
+                if k == 3 and eng == "tc":
+                    continue
+                qs.qs_set_tensor_cores(h, flag)
+                qs.qs_apply_dense(h, [], tg, U)
+                ts = []
+                for _ in range(3):
+                    a, b = _events(torch)
+                    a.record(stream)
+                    qs.qs_apply_dense(h, [], tg, U)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(a.elapsed_time(b))
+                ms = statistics.median(ts)
+                gbs = 2 * 8 * 2 ** n / (ms * 1e-3) / 1e9
+                v = {"ms": ms, "gbs": gbs, "tflops": 8 * 2 ** k * 2 ** n / (ms * 1e-3) / 1e12}
+                if eng == "tc":
+                    v["tensor_tflops"] = 24 * 2 ** k * 2 ** n / (ms * 1e-3) / 1e12
+                    if k == 5 and (best is None or gbs > best[1]["gbs"]):
+                        best = (label, v)
+                res["launches"][f"k{k}_{label}_{eng}"] = v
+    qs.qs_set_tensor_cores(h, 1)
+    label, v = best
+    res["roofline_tc_k5"] = {"bound": "hbm", "targets": label, "achieved": v["gbs"], "peak": peak, "unit": "GB/s",
+                             "frac": v["gbs"] / peak, "peak_source": peak_src,
+                             "tensor_tflops": v["tensor_tflops"], "tensor_peak_tflops": tpeak,
+                             "tensor_frac": v["tensor_tflops"] / tpeak, "tensor_peak_source": tpeak_src}
+    # Sampled parity of one k = 5 tensor-core launch from the seeded input.
+    dev.copy_(torch.from_numpy(psi64.view(np.float32)))
+    tg, cs = [n - 1, 3, 1, 18, 10], [0, n - 5]
+    U = W.haar_unitary(32, rng)
+    qs.qs_apply_dense(h, cs, tg, U)
+    pos = sorted(tg + cs)
+    groups = rng.integers(0, 1 << (n - 7), size=256)
+    offs = [sum(1 << tg[j] for j in range(5) if (s >> j) & 1) for s in range(32)]
+    idx = []
+    for g in groups.tolist():
+        b = g
+        for p_ in pos:
+            b = ((b >> p_) << (p_ + 1)) | (b & ((1 << p_) - 1))
+        for c in cs:
+            b |= 1 << c
+        idx += [b | o for o in offs]
+    idx = np.array(idx, dtype=np.uint64)
+    out = np.empty(idx.size, dtype=np.complex64)
+    qs.qs_gather(h, idx, out)
+    xin = psi64[idx.astype(np.int64)].astype(np.complex128).reshape(-1, 32)
+    got = out.astype(np.complex128).reshape(-1, 32)
+    want = xin @ U.T
+    bound = np.abs(xin) @ np.abs(U).T
+    res["tc_k5_sampled_err_over_fp32_bound"] = float(np.max(np.abs(got - want) / ((4 * 32 + 8) * 2.0 ** -24 * bound)))
+    res["tc_k5_sample"] = "256 groups of a 5-target, 2-control gate, each against U x in double on its 32 amplitudes"
+    qs.qs_destroy(h)
+    del dev
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_extra_workload(args):
     import torch
 
@@ -729,7 +822,13 @@ def run_extra_workload(args):
     build.build()
     from paper_2506_09198_gb300 import qs
 
-    if args.workload == "circuits":
+    if args.workload == "dense":
+        res = measure_dense_k(qs, torch, W.random_state(args.n, SEED_STATE))
+        line = {"metric": "dense 5-target gate on the tensor cores: HBM GB/s per launch vs peak",
+                "value": res["roofline_tc_k5"]["achieved"], "unit": "GB/s", "higher_is_better": True,
+                "config": {"workload": f"dense 3..5-target gates on a {args.n}-qubit complex64 state"},
+                "detail": res}
+    elif args.workload == "circuits":
         res = measure_circuits(qs, torch, args.n)
         line = {"metric": "fused circuits: RQC-20 and QFT device time, complex128 vs complex64",
                 "value": res["rqc20_c64"]["fused_ms"], "unit": "ms", "higher_is_better": False,
@@ -813,6 +912,14 @@ def summarize_extras(ex, peak):
                                "err": sv[d].get("max_err_vs_closed_form")}
         s["serve_fid_c64"] = sv.get("c64_vs_c128_state_fidelity", {}).get("min")
         s["serve_gpu_busy_pct"] = {d: (sv[d]["capacity"].get("gpu_busy") or {}).get("mean_pct") for d in ("c128", "c64")}
+    dk = ex.get("dense_k_30q_c64")
+    if dk:
+        rf = dk["roofline_tc_k5"]
+        s["dense_k5_30q_c64"] = {"tc_gbs": r(rf["achieved"]), "tc_frac": r(rf["frac"], 3),
+                                 "tc_tensor_frac": r(rf["tensor_frac"], 3),
+                                 "cuda_core_gbs": r(max(v["gbs"] for key, v in dk["launches"].items()
+                                                        if key.startswith("k5_") and key.endswith("cuda_cores"))),
+                                 "err_over_bound": r(dk["tc_k5_sampled_err_over_fp32_bound"], 3)}
     sp = ex.get("split_32q_c128")
     if sp:
         s["split_32q_gbs"] = {"local": r(sp["local_gate_q20"]["gbs"]), "global": r(sp["global_gate_swap_in"]["gbs"])}
@@ -967,6 +1074,8 @@ def run_ours(args):
         if "variants" in want:
             extras["sweep_fp64"] = measure_sweep_variant(qs, torch, n, "c128", "fp64", 1)
             extras["sweep_c64"] = measure_sweep_variant(qs, torch, n, "c64", "df", 3)
+        if "dense" in want and n == 30 and not c64:
+            extras["dense_k_30q_c64"] = measure_dense_k(qs, torch, psi_host)
         if "circuits" in want:
             extras["circuits_32q"] = measure_circuits(qs, torch, 32, fused_only=True)
         if "batch" in want:

@@ -81,16 +81,22 @@ float tf32_round_host(float x) {
 // ---------------------------------------------------------------------------
 // Tensor-core kernel
 // ---------------------------------------------------------------------------
-constexpr int kTcRows = 128;     // groups per tile: the MMA's M
-constexpr int kTcThreads = 256;  // 8 warps gather and scatter; warps 0-3 read the accumulator
+constexpr int kTcRows = 128;  // groups per tile: the MMA's M
+// Warp roles: 0-7 read the accumulator and store (warp w reads TMEM lane
+// quarter w % 4, column half w / 4), 8-15 load and split amplitudes into the
+// A stages, 16 issues the MMAs (one thread).
+constexpr int kTcEpiWarps = 8, kTcProdWarps = 8;
+constexpr int kTcEpiThreads = 32 * kTcEpiWarps, kTcProdThreads = 32 * kTcProdWarps;
+constexpr int kTcMmaWarp = kTcEpiWarps + kTcProdWarps;
+constexpr int kTcThreads = 32 * (kTcMmaWarp + 1);
 
 // The host orders the targets by position (and permutes U to match), so bit
 // 0 of the sub-register value s is the lowest target: the amplitudes s and
 // s + 1 of a group are the columns 4j..4j+3 of its A row, one 16-byte chunk.
-// Each thread moves such pairs.  A tile's pairs are numbered by a local index
-// whose bits are the other target bits and up to 7 row bits, in ascending
-// address order: thread tid takes pairs tid + 256 i, its bits 0-7 mapped by
-// lam_addr / lam_sr, i by the step tables; each maps to address bits and to
+// Threads move such pairs.  A tile's pairs are numbered by a local index whose
+// bits are the other target bits and up to 7 row bits, in ascending address
+// order.  Producer (and epilogue) thread t takes pairs t + 256 i, t's bits
+// 0-7 mapped by lam_* and i by step_*; each maps to address bits and to
 // (row, s), packed as row << 8 | s.
 struct TcParams {
   uint64_t n_tiles;
@@ -114,25 +120,27 @@ static_assert(sizeof(TcParams) < 30000, "kernel parameter space");
 // Operands in the K-major layout with the 128-byte swizzle: a row's K = 32
 // TF32 values of one atom column are 128 bytes, 8 rows make a 1024-byte atom,
 // and 16-byte chunk j of row r sits at chunk j ^ (r % 8).  K = 64 takes two
-// atom columns, each all rows deep.
+// atom columns, each all rows deep.  Two A stages and two TMEM accumulators;
+// the output stage is the epilogue's own.
 template <int KQ>
 struct TcShape {
   static constexpr int D = 1 << KQ;
   static constexpr int K = 2 * D;  // reals per row; the MMA's N and K
   static_assert(K == 32 || K == 64, "whole 128-byte swizzle atoms along K");
-  static constexpr int kAtomsK = K / 32;
   static constexpr uint32_t kABytes = kTcRows * K * 4;  // one A operand
   static constexpr uint32_t kBBytes = K * K * 4;        // one B operand
-  static constexpr uint32_t kOffAlo = kABytes;
-  static constexpr uint32_t kOffBhi = 2 * kABytes;
-  static constexpr uint32_t kOffBlo = 2 * kABytes + kBBytes;
-  static constexpr uint32_t kOffBar = 2 * kABytes + 2 * kBBytes;
-  static constexpr uint32_t kSmem = kOffBar + 32;
-  static constexpr uint32_t kCols = (uint32_t)K;           // TMEM columns (power of two >= 32)
-  static constexpr int kStageStride = D + 2;               // float2 per staged row (16-byte rows, padded)
-  static constexpr int kPairs = kTcRows * D / 2 / kTcThreads;  // pairs per thread per tile
-  static_assert(kTcRows * kStageStride * 8 <= 2 * kABytes, "output stage fits the A operands");
-  static_assert(kPairs <= 8, "step tables");
+  static constexpr uint32_t kStageA = 2 * kABytes;      // head + remainder of one stage
+  static constexpr uint32_t kOffBhi = 2 * kStageA;
+  static constexpr uint32_t kOffBlo = kOffBhi + kBBytes;
+  static constexpr int kStageStride = D + 2;  // float2 per staged output row (16-byte rows, padded)
+  static constexpr uint32_t kOffOut = kOffBlo + kBBytes;
+  static constexpr uint32_t kOffBar = kOffOut + kTcRows * kStageStride * 8;  // 8 mbarriers
+  static constexpr uint32_t kSmem = kOffBar + 80;                            // + TMEM address slot
+  static constexpr uint32_t kCols = 2 * (uint32_t)K;  // TMEM: two accumulators (power of two >= 32)
+  static constexpr int kPairs = kTcRows * D / 2 / kTcProdThreads;  // per producer / epilogue thread per tile
+  static_assert(kTcProdThreads == kTcEpiThreads, "one set of index tables");
+  static_assert(kPairs >= 1 && kPairs <= 8, "step tables");
+  static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
 };
 
 // Byte offset of element (row, col) of a swizzled K-major operand of `rows`
@@ -150,10 +158,11 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
          (2ull << 61);
 }
 
+// Round to the nearest TF32 value (ties away from zero) with two integer
+// operations: add half of the dropped 13 bits' range to the magnitude, then
+// clear them (finite inputs far below FLT_MAX).
 __device__ __forceinline__ float tf32_round(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
@@ -192,31 +201,56 @@ __device__ __forceinline__ uint64_t tile_base(uint64_t tile, const TcParams& p) 
   return g | p.fixed_mask;
 }
 
-// One CTA per tile at a time (persistent over tiles): gather the tile's
-// groups into the A operands (split into TF32 head and remainder), one
-// thread issues the MMAs and commits them to an mbarrier, the next tile's
-// amplitudes are loaded while they run, then warps 0-3 read the accumulator
-// rows (lane = row) into a padded staging area and all threads scatter it.
+// Group-wide barrier and AND-reduction among the epilogue warps (named
+// barrier 1, 256 threads).
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kTcEpiThreads) : "memory"); }
+__device__ __forceinline__ bool epi_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kTcEpiThreads)
+      : "memory");
+  return r != 0;
+}
+
+// Persistent over tiles (tile j of this CTA: blockIdx.x + j gridDim.x),
+// warp-specialized, with mbarriers between the roles and no CTA-wide
+// barrier in the loop:
+//   producers  wait empty[s], split the amplitudes held in registers into A
+//              stage s, arrive on full[s], then load tile j + 1 into
+//              registers;
+//   MMA thread waits full[s] and acc_empty[s], issues the three TF32
+//              products into accumulator s, commits to empty[s] and
+//              acc_full[s];
+//   epilogue   waits acc_full[s], reads its half rows (lane = row), arrives
+//              on acc_empty[s], and stores the rows through the output
+//              stage (in address order);
+// with s = j % 2.  Every wait is bounded: on expiry (or once another thread
+// recorded an error) a role leaves its loop and the others' waits then run
+// out too; the MMA thread waits (bounded) for its last commit so that no MMA
+// is in flight, and the accumulator is freed after the final barrier.
 template <int KQ>
-__global__ void __launch_bounds__(kTcThreads, 2)
+__global__ void __launch_bounds__(kTcThreads, 1)
     k_dense_tc(float2* __restrict__ psi, const __grid_constant__ TcParams p, uint32_t* __restrict__ err) {
   using S = TcShape<KQ>;
   constexpr int D = S::D, K = S::K, E = S::kPairs;
   // The swizzle follows address bits 4-9, so the operands start on
   // 1024-byte boundaries.  The dynamic shared memory (no static shared
   // memory here) starts on one; were it not, the kernel records device
-  // error code 3 and returns before touching memory.  No padding is
-  // allocated for it: 64 more bytes per CTA would leave room for one CTA
-  // per SM instead of two.
+  // error code 3 and returns before touching memory.
   extern __shared__ __align__(1024) unsigned char smem[];
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (smem_addr(smem) & 1023u) {
     if (tid == 0) atomicCAS(err, 0u, 3u);
     return;
   }
   const uint32_t base = smem_addr(smem);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::kOffBar);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S::kOffBar + 16);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::kOffBar);
+  uint64_t* empty = full + 2;
+  uint64_t* acc_full = full + 4;
+  uint64_t* acc_empty = full + 6;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S::kOffBar + 64);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
@@ -225,12 +259,17 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(bar, 1);
+    for (int st = 0; st < 2; ++st) {
+      mbar_init(full + st, kTcProdThreads);
+      mbar_init(empty + st, 1);
+      mbar_init(acc_full + st, 1);
+      mbar_init(acc_empty + st, kTcEpiThreads);
+    }
     mbar_fence_init();
   }
-  // Zero the A operands (rows beyond a small state's groups stay zero) and
+  // Zero both A stages (rows beyond a small state's groups stay zero) and
   // build R's TF32 parts (the B operand: N = K rows, K-major).
-  for (uint32_t o = (uint32_t)tid * 16u; o < 2 * S::kABytes; o += kTcThreads * 16u)
+  for (uint32_t o = (uint32_t)tid * 16u; o < 2 * S::kStageA; o += kTcThreads * 16u)
     *reinterpret_cast<float4*>(smem + o) = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int e = tid; e < K * K; e += kTcThreads) {
     const int row = e / K, col = e % K;
@@ -250,138 +289,159 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     *reinterpret_cast<float*>(smem + S::kOffBhi + off) = h;
     *reinterpret_cast<float*>(smem + S::kOffBlo + off) = l;
   }
-  // This thread's part of every tile-local pair index.
-  uint64_t a_t = 0;
-  uint32_t sr_t = 0;
-#pragma unroll
-  for (int b = 0; b < 8; ++b)
-    if ((tid >> b) & 1) {
-      a_t |= p.lam_addr[b];
-      sr_t |= p.lam_sr[b];
-    }
+  fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const uint64_t stride = gridDim.x;
 
-  // Instruction descriptor: FP32 accumulator (bits 4-5 = 1), TF32 A and B
-  // (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
-  // M >> 4 at bit 24.
-  constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(K >> 3) << 17) |
-                             ((uint32_t)(kTcRows >> 4) << 24);
-  float4* stage = reinterpret_cast<float4*>(smem);  // row r: (D + 2) / 2 float4, pairs (s, s + 1)
-  constexpr int kStage4 = S::kStageStride / 2;
-
-  float4 x[E];
-  auto load_tile = [&](uint64_t t) {
-    const uint64_t tb = tile_base(t, p) | a_t;
+  if (warp >= kTcEpiWarps && warp < kTcMmaWarp) {
+    // ---- producers ----
+    const int t = tid - kTcEpiThreads;
+    uint64_t a_t = 0;
+    uint32_t sr_t = 0;
 #pragma unroll
-    for (int i = 0; i < E; ++i)
-      if (tid + i * kTcThreads < p.npairs) {
-        const uint64_t a = tb | p.step_addr[i];
-        if (p.pair_vec) {
-          x[i] = *reinterpret_cast<const float4*>(psi + a);
-        } else {
-          const float2 u = psi[a], v = psi[a | p.pair_bit];
-          x[i] = make_float4(u.x, u.y, v.x, v.y);
+    for (int b = 0; b < 8; ++b)
+      if ((t >> b) & 1) {
+        a_t |= p.lam_addr[b];
+        sr_t |= p.lam_sr[b];
+      }
+    float4 x[E];
+    auto load_tile = [&](uint64_t tl) {
+      const uint64_t tb = tile_base(tl, p) | a_t;
+#pragma unroll
+      for (int i = 0; i < E; ++i)
+        if (t + i * kTcProdThreads < p.npairs) {
+          const uint64_t a = tb | p.step_addr[i];
+          if (p.pair_vec) {
+            x[i] = *reinterpret_cast<const float4*>(psi + a);
+          } else {
+            const float2 u = psi[a], v = psi[a | p.pair_bit];
+            x[i] = make_float4(u.x, u.y, v.x, v.y);
+          }
         }
-      }
-  };
-
-  uint64_t tile = blockIdx.x;
-  if (tile < p.n_tiles) load_tile(tile);
-  uint32_t phase = 0;
-  for (; tile < p.n_tiles; tile += gridDim.x) {
+    };
+    uint64_t tile = blockIdx.x;
+    if (tile < p.n_tiles) load_tile(tile);
+    for (uint32_t j = 0; tile < p.n_tiles; ++j, tile += stride) {
+      const int st = (int)(j & 1u);
+      if (!mbar_wait(empty + st, ((j >> 1) & 1u) ^ 1u, err, p.wait_ns)) break;
+      unsigned char* a_hi = smem + st * S::kStageA;
 #pragma unroll
-    for (int i = 0; i < E; ++i)
-      if (tid + i * kTcThreads < p.npairs) {
-        const uint32_t sr = sr_t | p.step_sr[i];
-        const uint32_t off = sw128_off((int)(sr >> 8), 2 * (int)(sr & 0xFFu), kTcRows);
-        const float4 h = make_float4(tf32_round(x[i].x), tf32_round(x[i].y), tf32_round(x[i].z), tf32_round(x[i].w));
-        *reinterpret_cast<float4*>(smem + off) = h;
-        *reinterpret_cast<float4*>(smem + S::kOffAlo + off) =
-            make_float4(tf32_round(x[i].x - h.x), tf32_round(x[i].y - h.y), tf32_round(x[i].z - h.z),
-                        tf32_round(x[i].w - h.w));
-      }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (tid == 0) {
-      // Three products, small ones first; K / 8 MMAs of K-depth 8 (32 bytes
-      // of a 128-byte swizzled row) each.
-      uint32_t acc = 0;
-#pragma unroll
-      for (int prod = 0; prod < 3; ++prod) {
-        const uint32_t a = base + (prod == 0 ? S::kOffAlo : 0u);
-        const uint32_t b = base + (prod == 1 ? S::kOffBlo : S::kOffBhi);
-#pragma unroll
-        for (int ks = 0; ks < K / 8; ++ks) {
-          const uint32_t within = (uint32_t)(ks & 3) * 32u, atom = (uint32_t)(ks >> 2);
-          tc_mma(tmem, smem_desc_sw128(a + atom * (kTcRows * 128u) + within),
-                 smem_desc_sw128(b + atom * (uint32_t)(K * 128) + within), idesc, acc);
-          acc = 1;
+      for (int i = 0; i < E; ++i)
+        if (t + i * kTcProdThreads < p.npairs) {
+          const uint32_t sr = sr_t | p.step_sr[i];
+          const uint32_t off = sw128_off((int)(sr >> 8), 2 * (int)(sr & 0xFFu), kTcRows);
+          const float4 h =
+              make_float4(tf32_round(x[i].x), tf32_round(x[i].y), tf32_round(x[i].z), tf32_round(x[i].w));
+          *reinterpret_cast<float4*>(a_hi + off) = h;
+          *reinterpret_cast<float4*>(a_hi + S::kABytes + off) =
+              make_float4(tf32_round(x[i].x - h.x), tf32_round(x[i].y - h.y), tf32_round(x[i].z - h.z),
+                          tf32_round(x[i].w - h.w));
         }
-      }
-      tc_commit(smem_addr(bar));
+      fence_async_smem();
+      mbar_arrive(full + st);
+      if (tile + stride < p.n_tiles) load_tile(tile + stride);
     }
-    const uint64_t next = tile + gridDim.x;
-    if (next < p.n_tiles) load_tile(next);
-    // Bounded wait for the MMAs by warp 0 (the others wait at the barrier
-    // without taking issue slots); on expiry every thread agrees, and thread
-    // 0 drains the MMAs still in flight (they read and write this CTA's own
-    // memory and complete) before the accumulator is freed.
-    bool done = true;
-    if (warp == 0) {
-      done = mbar_try(bar, phase);
-      if (!done) {
+    __syncwarp();
+  } else if (warp == kTcMmaWarp) {
+    // ---- MMA issue (one thread) ----
+    if (lane == 0) {
+      // Instruction descriptor: FP32 accumulator (bits 4-5 = 1), TF32 A and
+      // B (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at
+      // bit 17, M >> 4 at bit 24.
+      constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(K >> 3) << 17) |
+                                 ((uint32_t)(kTcRows >> 4) << 24);
+      int last = -1;  // accumulator of the last commit
+      uint32_t last_parity = 0;
+      uint64_t tile = blockIdx.x;
+      for (uint32_t j = 0; tile < p.n_tiles; ++j, tile += stride) {
+        const int st = (int)(j & 1u);
+        const uint32_t parity = (j >> 1) & 1u;
+        if (!mbar_wait(full + st, parity, err, p.wait_ns)) break;
+        if (!mbar_wait(acc_empty + st, parity ^ 1u, err, p.wait_ns)) break;
+        tc_fence_after();
+        // Three products, small ones first; K / 8 MMAs of K-depth 8 (32
+        // bytes of a 128-byte swizzled row) each.
+        uint32_t acc = 0;
+        const uint32_t d_tmem = tmem + (uint32_t)(st * K);
+#pragma unroll
+        for (int prod = 0; prod < 3; ++prod) {
+          const uint32_t a = base + (uint32_t)st * S::kStageA + (prod == 0 ? S::kABytes : 0u);
+          const uint32_t b = base + (prod == 1 ? S::kOffBlo : S::kOffBhi);
+#pragma unroll
+          for (int ks = 0; ks < K / 8; ++ks) {
+            const uint32_t within = (uint32_t)(ks & 3) * 32u, atom = (uint32_t)(ks >> 2);
+            tc_mma(d_tmem, smem_desc_sw128(a + atom * (kTcRows * 128u) + within),
+                   smem_desc_sw128(b + atom * (uint32_t)(K * 128) + within), idesc, acc);
+            acc = 1;
+          }
+        }
+        tc_commit(smem_addr(empty + st));
+        tc_commit(smem_addr(acc_full + st));
+        last = st;
+        last_parity = parity;
+      }
+      // No MMA may be in flight when the accumulator is freed.
+      if (last >= 0) {
         const uint64_t t0 = global_ns();
-        while (!(done = mbar_try(bar, phase)))
-          if (global_ns() - t0 > p.wait_ns) break;
-      }
-    }
-    if (__syncthreads_or(!done)) {
-      if (tid == 0) {
-        atomicCAS(err, 0u, 1u);
-        const uint64_t t0 = global_ns();
-        while (!mbar_try(bar, phase) && global_ns() - t0 < kDrainNs) {
+        while (!mbar_try(acc_full + last, last_parity) && global_ns() - t0 < kDrainNs) {
         }
       }
-      break;
     }
-    phase ^= 1u;
-    tc_fence_after();
-    if (warp < 4) {
-      const int row = warp * 32 + (tid & 31);
-      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    __syncwarp();
+  } else {
+    // ---- epilogue (warps 0-7; warp w reads lanes 32 (w % 4) + lane, column half w / 4) ----
+    constexpr int kOut4 = S::kStageStride / 2;
+    constexpr int kHalf = K / 2;
+    float4* out = reinterpret_cast<float4*>(smem + S::kOffOut);  // row r: pairs (s, s + 1)
+    const int t = tid;
+    uint64_t a_t = 0;
+    uint32_t sr_t = 0;
 #pragma unroll
-      for (int c0 = 0; c0 < K; c0 += 16) {
-        float v[16];
-        tc_ld16(lane_addr + (uint32_t)c0, v);
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          stage[row * kStage4 + (c0 >> 2) + j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    for (int b = 0; b < 8; ++b)
+      if ((t >> b) & 1) {
+        a_t |= p.lam_addr[b];
+        sr_t |= p.lam_sr[b];
       }
-    }
-    tc_fence_before();
-    __syncthreads();
-    {
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = quarter * 32 + lane;
+    uint64_t tile = blockIdx.x;
+    for (uint32_t j = 0; tile < p.n_tiles; ++j, tile += stride) {
+      const int st = (int)(j & 1u);
+      const bool ok = mbar_wait(acc_full + st, (j >> 1) & 1u, err, p.wait_ns);
+      __syncwarp();  // the barrier reduction and TMEM loads below are warp-aligned
+      if (!epi_all(ok)) break;
+      tc_fence_after();
+      float v[kHalf];
+#pragma unroll
+      for (int c0 = 0; c0 < kHalf; c0 += 16)
+        tc_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(st * K + half * kHalf + c0), v + c0);
+      tc_fence_before();
+      mbar_arrive(acc_empty + st);
+      // The previous tile's stores have read the output stage.
+      epi_sync();
+#pragma unroll
+      for (int q = 0; q < kHalf / 4; ++q)
+        out[row * kOut4 + half * (kHalf / 4) + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      epi_sync();
       const uint64_t tb = tile_base(tile, p) | a_t;
 #pragma unroll
       for (int i = 0; i < E; ++i)
-        if (tid + i * kTcThreads < p.npairs) {
+        if (t + i * kTcEpiThreads < p.npairs) {
           const uint32_t sr = sr_t | p.step_sr[i];
-          const float4 v = stage[(int)(sr >> 8) * kStage4 + (int)((sr & 0xFFu) >> 1)];
+          const float4 w = out[(int)(sr >> 8) * kOut4 + (int)((sr & 0xFFu) >> 1)];
           const uint64_t a = tb | p.step_addr[i];
           if (p.pair_vec) {
-            *reinterpret_cast<float4*>(psi + a) = v;
+            *reinterpret_cast<float4*>(psi + a) = w;
           } else {
-            psi[a] = make_float2(v.x, v.y);
-            psi[a | p.pair_bit] = make_float2(v.z, v.w);
+            psi[a] = make_float2(w.x, w.y);
+            psi[a | p.pair_bit] = make_float2(w.z, w.w);
           }
         }
     }
-    __syncthreads();
+    __syncwarp();
   }
   __syncthreads();
   if (warp == 0) {
@@ -477,7 +537,6 @@ qs_status launch_cuda_core(qs_state s, const DenseGeom& g, const double* U) {
 
 template <int KQ>
 qs_status launch_tensor_core(qs_state s, const DenseGeom& g, const double* U) {
-  using S = TcShape<KQ>;
   constexpr int D = 1 << KQ;
   static thread_local TcParams p;
   std::memset(&p, 0, sizeof(p));
@@ -499,24 +558,30 @@ qs_status launch_tensor_core(qs_state s, const DenseGeom& g, const double* U) {
       if ((v >> j) & 1) u |= 1 << order[j];
     return u;
   };
-  p.pair_bit = 1ull << g.targets[order[0]];
-  p.pair_vec = g.targets[order[0]] == 0 ? 1 : 0;
+  const int low_target = g.targets[order[0]];
+  p.pair_bit = 1ull << low_target;
+  p.pair_vec = low_target == 0 ? 1 : 0;
   // Pair-index bits in ascending address order: sorted targets 1..k-1 map
   // to s bits 1..k-1, the r-th lowest free position to row bit r.
   std::vector<std::pair<int, uint32_t>> bits;
   for (int j = 1; j < KQ; ++j) bits.push_back({g.targets[order[j]], 1u << j});
   for (int r = 0; r < rb; ++r) bits.push_back({g.free_pos[r], (1u << r) << 8});
   std::sort(bits.begin(), bits.end());
-  for (int b = 0; b < (int)bits.size() && b < 8; ++b) {
-    p.lam_addr[b] = 1ull << bits[b].first;
-    p.lam_sr[b] = bits[b].second;
+  // 8 thread bits, then up to 3 step bits.
+  for (int b = 0; b < (int)bits.size(); ++b) {
+    const uint64_t ab = 1ull << bits[b].first;
+    const uint32_t sb = bits[b].second;
+    if (b < 8) {
+      p.lam_addr[b] = ab;
+      p.lam_sr[b] = sb;
+    } else {
+      for (int i = 0; i < 8; ++i)
+        if ((i >> (b - 8)) & 1) {
+          p.step_addr[i] |= ab;
+          p.step_sr[i] |= sb;
+        }
+    }
   }
-  for (int i = 0; i < 8; ++i)
-    for (int b = 8; b < (int)bits.size(); ++b)
-      if ((i >> (b - 8)) & 1) {
-        p.step_addr[i] |= 1ull << bits[b].first;
-        p.step_sr[i] |= bits[b].second;
-      }
   for (int r = 0; r < D; ++r)
     for (int c = 0; c < D; ++c)
       for (int part = 0; part < 2; ++part) {
@@ -528,21 +593,19 @@ qs_status launch_tensor_core(qs_state s, const DenseGeom& g, const double* U) {
   p.wait_ns = wait_limit_ns();
   uint32_t* err = error_word(s);
   if (!err) return fail(QS_ERR_CUDA, "device error word unavailable");
+  using S = TcShape<KQ>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
     attr_err = cudaFuncSetAttribute(k_dense_tc<KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
-    // All of the unified L1 / shared array as shared memory: two CTAs per SM
-    // at k = 5 (the default split leaves room for one).
+    // All of the unified L1 / shared array as shared memory.
     if (attr_err == cudaSuccess)
       attr_err = cudaFuncSetAttribute(k_dense_tc<KQ>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       (int)cudaSharedmemCarveoutMaxShared);
   });
   if (attr_err != cudaSuccess) return cuda_fail(attr_err, "k_dense_tc set-up");
-  // Two CTAs per SM: the launch bounds keep the registers within half the
-  // file and two copies of the shared memory fit (the grid-stride loop over
-  // tiles stays correct with fewer resident).
-  const uint64_t cap = (uint64_t)sm_count(s->device) * 2;
+  // One CTA per SM (its pipeline holds up to four tiles).
+  const uint64_t cap = (uint64_t)sm_count(s->device);
   const unsigned grid = (unsigned)(p.n_tiles < cap ? p.n_tiles : cap);
   k_dense_tc<KQ><<<grid, kTcThreads, S::kSmem, s->stream>>>((float2*)s->psi, p, err);
   QS_CUDA(cudaGetLastError());

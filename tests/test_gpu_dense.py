@@ -241,3 +241,35 @@ def test_tensor_core_switch_arguments():
     with pytest.raises(q.QSError):
         q.qs_apply_dense(st.h, [0], [0, 1, 2], W.haar_unitary(8, W.rng_for(2)))  # control is a target
     st.close()
+
+
+@pytest.fixture
+def restore_wait_limit():
+    yield
+    qs().qs_set_wait_limit(2.0)
+
+
+def test_dense_tc_wait_runs_out_and_context_survives(restore_wait_limit):
+    """With a zero wait limit the tensor-core kernel's bounded mbarrier waits
+    give up: the state's next sync reports QS_ERR_TIMEOUT, the kernel has
+    freed its tensor memory and returned, and the same context then applies
+    the gate correctly."""
+    q = qs()
+    n = 20
+    tg = [0, 5, 9, 14, 19]
+    U = W.haar_unitary(32, W.rng_for(7700))
+    st = q.State(n, q.QS_C64)
+    q.qs_set_wait_limit(0.0)
+    for _ in range(4):
+        q.qs_apply_dense(st.h, [], tg, U)
+    q.qs_set_wait_limit(2.0)
+    with pytest.raises(q.QSError) as e:
+        st.sync()
+    assert e.value.status == q.QS_ERR_TIMEOUT
+    st.sync()  # reading the error cleared it
+    psi = W.random_state(n, W.rng_for(7701))
+    st.load(psi)
+    q.qs_apply_dense(st.h, [], tg, U)
+    got = st.read()
+    st.close()
+    check(got, stored_input(psi, "c64_tc"), [W.gk(tg, U)], "c64_tc", "after a timeout")
