@@ -734,7 +734,8 @@ def tf32_peak():
 def measure_dense_k(qs, torch, psi_host, seed=2540):
     """Dense gates on k = 3, 4, 5 targets (low, high and scattered positions)
     of a seeded state (the benchmark's 30-qubit one: 8 GiB) in complex64: device time
-    of one launch on the tensor cores (k = 4, 5) and on the FP32 CUDA cores,
+    of one launch on the tensor cores (mode 2; k = 3 runs as I (x) U on a
+    fourth target) and on the FP32 CUDA cores,
     algorithmic GB/s (one read and one write of the state), useful TFLOP/s
     (8 2^k real flops per amplitude) and, for the tensor cores, the pipe's
     TFLOP/s (three TF32 products: 24 2^k flops per amplitude).  Then sampled
@@ -755,9 +756,7 @@ def measure_dense_k(qs, torch, psi_host, seed=2540):
         U = W.haar_unitary(1 << k, rng)
         for label, tg in (("low", list(range(k))), ("high", list(range(n - k, n))),
                           ("scattered", [0, 7, 15, 22, n - 1][:k])):
-            for eng, flag in (("tc", 1), ("cuda_cores", 0)):
-                if k == 3 and eng == "tc":
-                    continue
+            for eng, flag in (("tc", 2), ("cuda_cores", 0)):
                 qs.qs_set_tensor_cores(h, flag)
                 qs.qs_apply_dense(h, [], tg, U)
                 ts = []
@@ -776,7 +775,7 @@ def measure_dense_k(qs, torch, psi_host, seed=2540):
                     if k == 5 and (best is None or gbs > best[1]["gbs"]):
                         best = (label, v)
                 res["launches"][f"k{k}_{label}_{eng}"] = v
-    qs.qs_set_tensor_cores(h, 1)
+    qs.qs_set_tensor_cores(h, 2)
     label, v = best
     res["roofline_tc_k5"] = {"bound": "hbm", "targets": label, "achieved": v["gbs"], "peak": peak, "unit": "GB/s",
                              "frac": v["gbs"] / peak, "peak_source": peak_src,

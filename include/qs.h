@@ -114,16 +114,20 @@ qs_status qs_destroy(qs_state s);
 
 qs_status qs_set_stream(qs_state s, void* cuda_stream);
 qs_status qs_set_math(qs_state s, qs_math math);
-/* Engine for complex64 dense gates on 4 and 5 targets (qs_apply_dense,
- * QS_GATE_UK); 3 targets always run on the FP32 CUDA cores, which keep up
- * with HBM there.
- * 1 (default): the tensor cores.  Each group of 2^k amplitudes is a row of a
- *   GEMM with the gate's real 2^(k+1) x 2^(k+1) form; operands are split into
- *   TF32 head and remainder and three products are summed in FP32, so the
- *   error stays at FP32's level (about 1e-7 relative to the gate's row norms).
- * 0: one FP32 FMA chain per output on the CUDA cores.
+/* Engine for complex64 dense gates on 3..5 targets (qs_apply_dense,
+ * QS_GATE_UK).  On the tensor cores each group of 2^k amplitudes is a row of
+ * a GEMM with the gate's real 2^(k+1) x 2^(k+1) form (3 or 4 targets: the
+ * 5-target form I (x) U with the lowest free qubits); operands are split into TF32 head
+ * and remainder and three products are summed in FP32, so the error stays at
+ * FP32's level (per amplitude within (4 d + 8) 2^-24 sum_c |U_rc||x_c|).  On
+ * the CUDA cores each output is one FP32 FMA chain.
+ * mode 1 (default): the tensor cores at 5 targets, and at 3 or 4 targets when
+ *   qubits 0 and 1 are both targets or controls (the CUDA-core kernel's
+ *   accesses are strided then); the CUDA cores otherwise.
+ * mode 2: the tensor cores wherever they apply (3 targets need 2 free qubits).
+ * mode 0: the CUDA cores.
  * complex128 states ignore it: they use FP64 FMA chains on the CUDA cores. */
-qs_status qs_set_tensor_cores(qs_state s, int enable);
+qs_status qs_set_tensor_cores(qs_state s, int mode);
 qs_status qs_num_qubits(qs_state s, int* n);
 qs_status qs_device_ptr(qs_state s, void** device_ptr);
 
@@ -172,9 +176,9 @@ qs_status qs_apply_ctrl(qs_state s, const int* ctrls, int nctrl, int target, con
  * each group of 2^k amplitudes sharing the other bits is multiplied by U
  * (Sec. II-B: a k-qubit gate is a 2^k x 2^k unitary on its index bits).
  * Diagonal and permutation matrices run as qs_apply_diag / qs_apply_perm;
- * dense matrices on 4 or 5 targets run on the tensor cores for complex64
- * states (qs_set_tensor_cores), on 3 targets on FP32 CUDA cores; complex128
- * states use FP64 CUDA cores. */
+ * dense matrices on 3..5 targets run on the tensor cores or the FP32 CUDA
+ * cores for complex64 states (qs_set_tensor_cores), on FP64 CUDA cores for
+ * complex128 states. */
 qs_status qs_apply_dense(qs_state s, const int* ctrls, int nctrl, const int* targets, int k, const double* U);
 
 /* Diagonal gate on k targets (1 <= k <= QS_MAX_TARGETS):

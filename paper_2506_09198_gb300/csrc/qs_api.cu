@@ -346,7 +346,7 @@ qs_status qs_set_math(qs_state s, qs_math math) {
 qs_status qs_set_tensor_cores(qs_state s, int enable) {
   qs_status st = check_state(s);
   if (st != QS_OK) return st;
-  if (enable != 0 && enable != 1) return fail(QS_ERR_ARG, "enable must be 0 or 1");
+  if (enable < 0 || enable > 2) return fail(QS_ERR_ARG, "tensor-core mode %d outside [0, 2]", enable);
   s->tensor_cores = enable;
   if (s->split) split_set_tensor_cores(s, enable);
   return QS_OK;

@@ -5,7 +5,8 @@
 //
 // Two kernels:
 //
-// k_dense_tc (complex64 states, k = 4 and 5 unless disabled): the
+// k_dense_tc (complex64 states, as the state's tensor-core mode selects; 3
+// and 4 targets run as the 5-target gate I (x) U on free qubits): the
 // fifth-generation tensor cores.  Over reals with (re, im) interleaved, the action on one
 // group is y = R x with the 2d x 2d real matrix
 //   R[2r][2c] = Re U[r][c],   R[2r][2c+1] = -Im U[r][c],
@@ -17,7 +18,7 @@
 // D = A_lo R_hi + A_hi R_lo + A_hi R_hi; the dropped A_lo R_lo is about
 // 2^-24 of the result, so the error stays at FP32's level.
 //
-// k_dense_k (complex64 at k = 3 or on request, complex128 always): one thread per group
+// k_dense_k (complex64 where the mode selects it, complex128 always): one thread per group
 // on the CUDA cores, U in shared memory (broadcast reads), the d outputs as
 // d-term FMA chains in FP32 (complex64) or FP64 (complex128).
 #include <algorithm>
@@ -619,11 +620,39 @@ qs_status launch_tensor_core(qs_state s, const DenseGeom& g, const double* U) {
 qs_status launch_dense_k(qs_state s, const int* targets, int k, uint64_t ctrl_mask, const double* U) {
   if (k < 3 || k > 5) return fail(QS_ERR_UNSUPPORTED, "dense gates on %d targets (at most 5)", k);
   const DenseGeom g = dense_geom(s, targets, k, ctrl_mask);
-  // The tensor cores take k = 4, 5 (rows of whole 128-byte swizzle atoms);
-  // at k = 3 the FP32 CUDA cores already keep up with HBM.
-  if (s->dtype == QS_C64 && s->tensor_cores && k >= 4) {
-    if (k == 4) return launch_tensor_core<4>(s, g, U);
-    return launch_tensor_core<5>(s, g, U);
+  if (s->dtype == QS_C64 && s->tensor_cores != 0) {
+    // The CUDA-core kernel's loads are strided when its consecutive groups
+    // are far apart, i.e. when qubits 0 and 1 are both targets or controls:
+    // then the tensor cores win at k = 3, 4 too (measured at 30 qubits: 4.8
+    // against 1.9-2.9 TB/s); otherwise the CUDA cores keep up with HBM there
+    // (4.8-5.7 TB/s).  At k = 5 the tensor cores always win.  Mode 2 takes
+    // the tensor cores wherever they apply.
+    const int low_free = g.free_pos.empty() ? 64 : g.free_pos[0];
+    const bool strided = low_free >= 2;
+    if (k == 5) return launch_tensor_core<5>(s, g, U);
+    if (strided || s->tensor_cores == 2) {
+      // Fewer targets run as the 5-target gate I (x) U on the lowest free
+      // qubits (new high bits of the index: block-diagonal, 2^(5-k) copies of
+      // U), at the 5-target kernel's rate; k = 4 without a free qubit runs on
+      // the 4-target kernel.
+      const int pad = 5 - k;
+      if ((int)g.free_pos.size() >= pad) {
+        int t5[5];
+        for (int j = 0; j < k; ++j) t5[j] = targets[j];
+        for (int j = 0; j < pad; ++j) t5[k + j] = g.free_pos[j];
+        const int d = 1 << k;
+        static thread_local double V[2 * 32 * 32];
+        std::memset(V, 0, sizeof(V));
+        for (int r = 0; r < 32; ++r)
+          for (int c = 0; c < 32; ++c)
+            if ((r >> k) == (c >> k)) {
+              V[2 * (r * 32 + c)] = U[2 * ((r & (d - 1)) * d + (c & (d - 1)))];
+              V[2 * (r * 32 + c) + 1] = U[2 * ((r & (d - 1)) * d + (c & (d - 1))) + 1];
+            }
+        return launch_tensor_core<5>(s, dense_geom(s, t5, 5, ctrl_mask), V);
+      }
+      if (k == 4) return launch_tensor_core<4>(s, g, U);
+    }
   }
   if (s->dtype == QS_C64) {
     if (k == 3) return launch_cuda_core<float, 3>(s, g, U);

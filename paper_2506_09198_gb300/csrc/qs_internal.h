@@ -11,8 +11,9 @@ struct qs_state_s {
   int n = 0;
   qs_dtype dtype = QS_C128;
   qs_math math = QS_MATH_DF;
-  // complex64 dense gates on 4 or 5 targets: tensor cores (1) or FP32 CUDA
-  // cores (0); qs_set_tensor_cores.
+  // complex64 dense gates on 3..5 targets: CUDA cores (0), tensor cores where
+  // they are faster (1), tensor cores wherever they apply (2);
+  // qs_set_tensor_cores.
   int tensor_cores = 1;
   void* psi = nullptr;  // device amplitudes
   bool owns = false;
@@ -93,9 +94,9 @@ qs_status run_gather(qs_state s, const uint64_t* idx, int64_t count, void* host_
 // classify the gate (identity, diagonal, phase on a pattern, X/Y move,
 // permutation, dense) and launch the cheapest kernel for it.
 qs_status dispatch_u1(qs_state s, int target, uint64_t ctrl_mask, const double* U);
-// Dense gate on 3..5 targets (qs_densek.cu): tensor cores for complex64
-// states at 4 or 5 targets unless the state disabled them, FP32 / FP64 CUDA
-// cores otherwise.
+// Dense gate on 3..5 targets (qs_densek.cu): tensor cores or FP32 CUDA
+// cores for complex64 states (the state's tensor-core mode), FP64 CUDA cores
+// for complex128.
 qs_status launch_dense_k(qs_state s, const int* targets, int k, uint64_t ctrl_mask, const double* U);
 qs_status dispatch_uk(qs_state s, const int* targets, int k, uint64_t ctrl_mask, const double* M);
 qs_status dispatch_diag(qs_state s, const int* targets, int k, uint64_t ctrl_mask, const double* d);

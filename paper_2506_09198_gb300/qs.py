@@ -233,8 +233,8 @@ def qs_apply_dense(h, ctrls, targets, U):
     _check(_lib.qs_apply_dense(h, pc, c.size, pt, t.size, p))
 
 
-def qs_set_tensor_cores(h, enable: int):
-    _check(_lib.qs_set_tensor_cores(h, int(enable)))
+def qs_set_tensor_cores(h, mode: int):
+    _check(_lib.qs_set_tensor_cores(h, int(mode)))
 
 
 def qs_apply_diag(h, targets, d):

@@ -1,8 +1,10 @@
 """Dense gates on 3..5 targets through the C ABI against the oracle.
 
-complex64 states run on the tensor cores at 4 and 5 targets (3xTF32 split,
-the default) or on the FP32 CUDA cores (3 targets, or qs_set_tensor_cores(0));
-complex128 states on FP64 CUDA cores.  Sizes span one group (n = k), a partial tile (fewer than 128
+complex64 states run on the tensor cores (3xTF32 split; mode 2 takes them
+wherever they apply: 3 and 4 targets as the 5-target gate I (x) U on free
+qubits, 4 targets on the 4-target kernel when no qubit is free), on the
+default mix (mode 1) or on the FP32 CUDA cores (mode 0); complex128 states on
+FP64 CUDA cores.  Sizes span one group (n = k), a partial tile (fewer than 128
 groups), many tiles and more tiles than resident CTAs; targets low, high and
 scattered (unsorted); 0-2 controls.
 
@@ -23,7 +25,7 @@ from gpu_common import C128_TOL, oracle_threads, qs
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["c64_tc", "c64_cc", "c128_df", "c128_fp64"]
+MODES = ["c64_tc", "c64_auto", "c64_cc", "c128_df", "c128_fp64"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -38,7 +40,7 @@ def make_state(n, mode, psi):
     q = qs()
     if mode.startswith("c64"):
         st = q.State(n, q.QS_C64)
-        q.qs_set_tensor_cores(st.h, 1 if mode == "c64_tc" else 0)
+        q.qs_set_tensor_cores(st.h, {"c64_tc": 2, "c64_auto": 1, "c64_cc": 0}[mode])
     else:
         st = q.State(n, q.QS_C128, q.QS_MATH_DF if mode == "c128_df" else q.QS_MATH_FP64)
     st.load(psi)
@@ -175,6 +177,8 @@ def test_dense_k_on_split_states(mode):
     rng = W.rng_for(7600)
     dt = q.QS_C64 if mode.startswith("c64") else q.QS_C128
     st = q.State.split(n, dt, g=2, hbm_segments=2)
+    if mode == "c64_tc":
+        q.qs_set_tensor_cores(st.h, 2)
     psi = W.random_state(n, rng)
     st.load(psi)
     x_in = stored_input(psi, mode)
@@ -234,7 +238,7 @@ def test_tensor_core_switch_arguments():
     q = qs()
     st = q.State(6, q.QS_C64)
     with pytest.raises(q.QSError):
-        q.qs_set_tensor_cores(st.h, 2)
+        q.qs_set_tensor_cores(st.h, 3)
     U = W.haar_unitary(64, W.rng_for(1))
     with pytest.raises(q.QSError):
         q.qs_apply_dense(st.h, [], [0, 1, 2, 3, 4, 5], U)  # 6 targets: above QS_MAX_DENSE
@@ -259,6 +263,7 @@ def test_dense_tc_wait_runs_out_and_context_survives(restore_wait_limit):
     tg = [0, 5, 9, 14, 19]
     U = W.haar_unitary(32, W.rng_for(7700))
     st = q.State(n, q.QS_C64)
+    q.qs_set_tensor_cores(st.h, 2)
     q.qs_set_wait_limit(0.0)
     for _ in range(4):
         q.qs_apply_dense(st.h, [], tg, U)
