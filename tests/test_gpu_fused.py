@@ -214,11 +214,13 @@ def test_fused_equals_unfused_many_tiles(mode):
     assert_close(b, a, mode, "fused vs gate-by-gate")
 
 
-def test_dense_three_qubit_gate_rejected():
+def test_dense_six_qubit_gate_rejected():
+    """Dense matrices go up to QS_MAX_DENSE (5) targets; a dense 6-target
+    matrix (neither diagonal nor a permutation) is rejected before any work."""
     q = qs()
-    st = new_state(6, "c128_df")
+    st = new_state(8, "c128_df")
     with pytest.raises(q.QSError) as e:
-        st.run([W.gk((0, 2, 4), W.haar_unitary(8, W.rng_for(1)))])
+        st.run([W.gk((0, 2, 4, 5, 6, 7), W.haar_unitary(64, W.rng_for(1)))])
     assert e.value.status == q.QS_ERR_UNSUPPORTED
     st.close()
 
