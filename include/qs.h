@@ -280,7 +280,10 @@ qs_status qs_autotune(qs_state s, const qs_circuit* c, int* best_max_fuse, doubl
  * fused whole-GPU blocks (qs_fuse_run).  The first state's stream first waits
  * for the work already queued on every other member's stream, and every
  * other member's stream then waits for the batch (events; the host does not
- * block).  The circuits are read before the call returns. */
+ * block).  The circuits are read before the call returns.  Every gate must fit
+ * a fused tile op (dense on at most 2 targets, diagonal or permutation on at
+ * most 8): a dense gate on 3..5 targets gives QS_ERR_UNSUPPORTED here (run it
+ * with qs_fuse_run or qs_apply_dense). */
 qs_status qs_batch_run(qs_state* states, const qs_circuit* const* circuits, int count, const qs_run_opts* opts);
 
 /* A compiled batch: the work of qs_batch_run compiled and captured as a CUDA
