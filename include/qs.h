@@ -126,7 +126,9 @@ qs_status qs_set_math(qs_state s, qs_math math);
  *   accesses are strided then); the CUDA cores otherwise.
  * mode 2: the tensor cores wherever they apply (3 targets need 2 free qubits).
  * mode 0: the CUDA cores.
- * complex128 states ignore it: they use FP64 FMA chains on the CUDA cores. */
+ * complex128 states ignore it: they run on the CUDA cores in their math mode
+ * (float-float: one lane per output row, TwoSum accumulation; FP64: FMA
+ * chains). */
 qs_status qs_set_tensor_cores(qs_state s, int mode);
 qs_status qs_num_qubits(qs_state s, int* n);
 qs_status qs_device_ptr(qs_state s, void** device_ptr);
@@ -177,8 +179,8 @@ qs_status qs_apply_ctrl(qs_state s, const int* ctrls, int nctrl, int target, con
  * (Sec. II-B: a k-qubit gate is a 2^k x 2^k unitary on its index bits).
  * Diagonal and permutation matrices run as qs_apply_diag / qs_apply_perm;
  * dense matrices on 3..5 targets run on the tensor cores or the FP32 CUDA
- * cores for complex64 states (qs_set_tensor_cores), on FP64 CUDA cores for
- * complex128 states. */
+ * cores for complex64 states (qs_set_tensor_cores), on the CUDA cores in the
+ * state's math mode for complex128 states. */
 qs_status qs_apply_dense(qs_state s, const int* ctrls, int nctrl, const int* targets, int k, const double* U);
 
 /* Diagonal gate on k targets (1 <= k <= QS_MAX_TARGETS):

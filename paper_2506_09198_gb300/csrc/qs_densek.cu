@@ -18,15 +18,21 @@
 // D = A_lo R_hi + A_hi R_lo + A_hi R_hi; the dropped A_lo R_lo is about
 // 2^-24 of the result, so the error stays at FP32's level.
 //
-// k_dense_k (complex64 where the mode selects it, complex128 always): one thread per group
-// on the CUDA cores, U in shared memory (broadcast reads), the d outputs as
-// d-term FMA chains in FP32 (complex64) or FP64 (complex128).
+// k_dense_k (complex64 where the mode selects it, complex128 in FP64
+// arithmetic): one thread per group on the CUDA cores, U in shared memory
+// (broadcast reads), the d outputs as d-term FMA chains in FP32 or FP64.
+//
+// k_dense_df (complex128 in float-float arithmetic, the default): one lane
+// per output row, inputs split to float-float once and shared through shared
+// memory, each row an anchored float-float accumulation.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
 
 #include "qs_internal.h"
+#include "qs_math.cuh"
 #include "qs_tile_dev.cuh"
 
 namespace qs {
@@ -514,6 +520,81 @@ __global__ void __launch_bounds__(128)
 }
 
 // ---------------------------------------------------------------------------
+// Float-float kernel
+// ---------------------------------------------------------------------------
+// A warp holds G = 32 / d groups; lane = g d + r computes output r of group g.
+// Each lane loads input r, splits it into float-float once and stages it in
+// shared memory (padded per group); lane r then accumulates sum_c U[r][c] x_c
+// over its group's staged inputs (TwoSum of the heads, exact product tails,
+// the rest in the tail sum: its error stays near 2^-43 of the row's partial
+// sums for 32 terms, where an anchored head sum, whose anchor must exceed the
+// row's coefficient sum times the largest input, loses 2^-38 of it) and
+// rounds to double.
+template <int KQ>
+struct DFDenseParams {
+  uint64_t n_groups;
+  int npos;
+  uint64_t high_mask[QS_MAX_QUBITS];
+  uint64_t fixed_mask;
+  uint64_t offs[1 << KQ];
+  // U[r][c] at [c][r] as (re_h, re_l, im_h, im_l); the kernel expands it
+  // into the two terms of the packed (re, im) product in shared memory.
+  float4 u[(1 << KQ) * (1 << KQ)];
+};
+
+template <int KQ>
+__global__ void __launch_bounds__(256) k_dense_df(double2* __restrict__ psi, const __grid_constant__ DFDenseParams<KQ> p) {
+  constexpr int D = 1 << KQ, G = 32 / D, kWarps = 256 / 32;
+  // (re_h, re_h, re_l, re_l) and (-im_h, im_h, -im_l, im_l) per coefficient.
+  __shared__ float4 ua[D * D], ub[D * D];
+  __shared__ float4 xs[kWarps][G * (D + 1)];  // per warp: (re_h, im_h, re_l, im_l) of each group's inputs
+  for (int i = threadIdx.x; i < D * D; i += blockDim.x) {
+    const float4 u = p.u[i];
+    ua[i] = make_float4(u.x, u.x, u.y, u.y);
+    ub[i] = make_float4(-u.z, u.z, -u.w, u.w);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int gl = lane / D, r = lane % D;
+  const uint64_t warps = (uint64_t)gridDim.x * kWarps;
+  const uint64_t off_r = p.offs[r];
+  for (uint64_t g0 = ((uint64_t)blockIdx.x * kWarps + w) * G; g0 < p.n_groups; g0 += warps * G) {
+    const uint64_t g = g0 + gl;
+    const bool ok = g < p.n_groups;
+    uint64_t b = g;
+    for (int j = 0; j < p.npos; ++j) b += b & p.high_mask[j];
+    b |= p.fixed_mask;
+    const double2 x = ok ? psi[b | off_r] : make_double2(0.0, 0.0);
+    float rh, rl, ih, il;
+    d2ff(x.x, rh, rl);
+    d2ff(x.y, ih, il);
+    xs[w][gl * (D + 1) + r] = make_float4(rh, ih, rl, il);
+    __syncwarp();
+    DF2Acc acc;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const float4 v = xs[w][gl * (D + 1) + c];
+      const float4 a4 = ua[c * D + r], b4 = ub[c * D + r];
+      DF2Term ta, tb;
+      ta.h = make_float2(a4.x, a4.y);
+      ta.hn = make_float2(-a4.x, -a4.y);
+      ta.l = make_float2(a4.z, a4.w);
+      tb.h = make_float2(b4.x, b4.y);
+      tb.hn = make_float2(-b4.x, -b4.y);
+      tb.l = make_float2(b4.z, b4.w);
+      if (c == 0)
+        acc.template first<false>(ta, make_float2(v.x, v.y), make_float2(v.z, v.w));
+      else
+        acc.template add<false>(ta, make_float2(v.x, v.y), make_float2(v.z, v.w));
+      acc.template add<false>(tb, make_float2(v.y, v.x), make_float2(v.w, v.z));
+    }
+    __syncwarp();  // every lane has read the staged inputs
+    if (ok)
+      psi[b | off_r] = make_double2(f2d_exact(acc.S.x) + f2d_exact(acc.C.x), f2d_exact(acc.S.y) + f2d_exact(acc.C.y));
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
 template <typename T, int KQ>
@@ -532,6 +613,32 @@ qs_status launch_cuda_core(qs_state s, const DenseGeom& g, const double* U) {
   const uint64_t cap = (uint64_t)sm_count(s->device) * 16;
   const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
   k_dense_k<T, KQ><<<grid, 128, 0, s->stream>>>((V*)s->psi, p);
+  QS_CUDA(cudaGetLastError());
+  return QS_OK;
+}
+
+template <int KQ>
+qs_status launch_float_float(qs_state s, const DenseGeom& g, const double* U) {
+  constexpr int D = 1 << KQ;
+  static thread_local DFDenseParams<KQ> p;
+  std::memset(&p, 0, sizeof(p));
+  p.n_groups = g.n_groups;
+  p.npos = g.ins.npos;
+  for (int j = 0; j < QS_MAX_QUBITS; ++j) p.high_mask[j] = g.ins.high_mask[j];
+  p.fixed_mask = g.ins.fixed_mask;
+  for (int v = 0; v < D; ++v) p.offs[v] = g.offs[v];
+  for (int r = 0; r < D; ++r)
+    for (int c = 0; c < D; ++c) {
+      const double re = U[2 * (r * D + c)], im = U[2 * (r * D + c) + 1];
+      const float rh = (float)re, ih = (float)im;
+      const float rl = (float)(re - (double)rh), il = (float)(im - (double)ih);
+      p.u[c * D + r] = make_float4(rh, rl, ih, il);
+    }
+  const uint64_t warps = (g.n_groups * D + 31) / 32;
+  const uint64_t blocks = (warps + 7) / 8;
+  const uint64_t cap = (uint64_t)sm_count(s->device) * 8;
+  const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
+  k_dense_df<KQ><<<grid, 256, 0, s->stream>>>((double2*)s->psi, p);
   QS_CUDA(cudaGetLastError());
   return QS_OK;
 }
@@ -658,6 +765,11 @@ qs_status launch_dense_k(qs_state s, const int* targets, int k, uint64_t ctrl_ma
     if (k == 3) return launch_cuda_core<float, 3>(s, g, U);
     if (k == 4) return launch_cuda_core<float, 4>(s, g, U);
     return launch_cuda_core<float, 5>(s, g, U);
+  }
+  if (s->math == QS_MATH_DF) {
+    if (k == 3) return launch_float_float<3>(s, g, U);
+    if (k == 4) return launch_float_float<4>(s, g, U);
+    return launch_float_float<5>(s, g, U);
   }
   if (k == 3) return launch_cuda_core<double, 3>(s, g, U);
   if (k == 4) return launch_cuda_core<double, 4>(s, g, U);
