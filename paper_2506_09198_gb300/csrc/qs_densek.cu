@@ -90,9 +90,11 @@ float tf32_round_host(float x) {
 // ---------------------------------------------------------------------------
 constexpr int kTcRows = 128;  // groups per tile: the MMA's M
 // Warp roles: 0-7 read the accumulator and store (warp w reads TMEM lane
-// quarter w % 4, column half w / 4), 8-15 load and split amplitudes into the
-// A stages, 16 issues the MMAs (one thread).
-constexpr int kTcEpiWarps = 8, kTcProdWarps = 8;
+// quarter w % 4, column half w / 4), 8-23 load and split amplitudes into the
+// A stages, 24 issues the MMAs (one thread).  The register file is four 16K
+// partitions (one per SM sub-partition); 25 warps leave 72 registers a
+// thread, enough for a producer to hold two tiles of loads in flight.
+constexpr int kTcEpiWarps = 8, kTcProdWarps = 16;
 constexpr int kTcEpiThreads = 32 * kTcEpiWarps, kTcProdThreads = 32 * kTcProdWarps;
 constexpr int kTcMmaWarp = kTcEpiWarps + kTcProdWarps;
 constexpr int kTcThreads = 32 * (kTcMmaWarp + 1);
@@ -102,9 +104,10 @@ constexpr int kTcThreads = 32 * (kTcMmaWarp + 1);
 // s + 1 of a group are the columns 4j..4j+3 of its A row, one 16-byte chunk.
 // Threads move such pairs.  A tile's pairs are numbered by a local index whose
 // bits are the other target bits and up to 7 row bits, in ascending address
-// order.  Producer (and epilogue) thread t takes pairs t + 256 i, t's bits
-// 0-7 mapped by lam_* and i by step_*; each maps to address bits and to
-// (row, s), packed as row << 8 | s.
+// order.  Producer thread t takes pairs t + 512 i (t's bits 0-8 mapped by
+// prod_*, i by prod_step_*), epilogue thread t pairs t + 256 i (bits 0-7 by
+// lam_*, i by step_*); each maps to address bits and to (row, s), packed as
+// row << 8 | s.
 struct TcParams {
   uint64_t n_tiles;
   int rb;      // row bits of a tile: 7, fewer when the state has fewer groups
@@ -118,6 +121,10 @@ struct TcParams {
   uint32_t lam_sr[8];
   uint64_t step_addr[8];
   uint32_t step_sr[8];
+  uint64_t prod_addr[9];
+  uint32_t prod_sr[9];
+  uint64_t prod_step_addr[4];
+  uint32_t prod_step_sr[4];
   float u_hi[2 * 32 * 32];  // U (targets in position order) as (re, im), rounded to TF32
   float u_lo[2 * 32 * 32];  // U - u_hi, rounded to TF32
   uint64_t wait_ns;
@@ -144,9 +151,10 @@ struct TcShape {
   static constexpr uint32_t kOffBar = kOffOut + kTcRows * kStageStride * 8;  // 8 mbarriers
   static constexpr uint32_t kSmem = kOffBar + 80;                            // + TMEM address slot
   static constexpr uint32_t kCols = 2 * (uint32_t)K;  // TMEM: two accumulators (power of two >= 32)
-  static constexpr int kPairs = kTcRows * D / 2 / kTcProdThreads;  // per producer / epilogue thread per tile
-  static_assert(kTcProdThreads == kTcEpiThreads, "one set of index tables");
-  static_assert(kPairs >= 1 && kPairs <= 8, "step tables");
+  static constexpr int kProdPairs = kTcRows * D / 2 / kTcProdThreads;  // per producer thread per tile
+  static constexpr int kEpiPairs = kTcRows * D / 2 / kTcEpiThreads;    // per epilogue thread per tile
+  static_assert(kTcProdThreads == 512 && kTcEpiThreads == 256, "index tables");
+  static_assert(kProdPairs >= 1 && kProdPairs <= 4 && kEpiPairs <= 8, "step tables");
   static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
 };
 
@@ -225,8 +233,8 @@ __device__ __forceinline__ bool epi_all(bool v) {
 // warp-specialized, with mbarriers between the roles and no CTA-wide
 // barrier in the loop:
 //   producers  wait empty[s], split the amplitudes held in registers into A
-//              stage s, arrive on full[s], then load tile j + 1 into
-//              registers;
+//              stage s, arrive on full[s], then load tile j + 2 into
+//              registers (tile j + 1's loads are in flight meanwhile);
 //   MMA thread waits full[s] and acc_empty[s], issues the three TF32
 //              products into accumulator s, commits to empty[s] and
 //              acc_full[s];
@@ -241,7 +249,7 @@ template <int KQ>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_dense_tc(float2* __restrict__ psi, const __grid_constant__ TcParams p, uint32_t* __restrict__ err) {
   using S = TcShape<KQ>;
-  constexpr int D = S::D, K = S::K, E = S::kPairs;
+  constexpr int D = S::D, K = S::K;
   // The swizzle follows address bits 4-9, so the operands start on
   // 1024-byte boundaries.  The dynamic shared memory (no static shared
   // memory here) starts on one; were it not, the kernel records device
@@ -305,22 +313,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   if (warp >= kTcEpiWarps && warp < kTcMmaWarp) {
     // ---- producers ----
+    constexpr int E = S::kProdPairs;
     const int t = tid - kTcEpiThreads;
     uint64_t a_t = 0;
     uint32_t sr_t = 0;
 #pragma unroll
-    for (int b = 0; b < 8; ++b)
+    for (int b = 0; b < 9; ++b)
       if ((t >> b) & 1) {
-        a_t |= p.lam_addr[b];
-        sr_t |= p.lam_sr[b];
+        a_t |= p.prod_addr[b];
+        sr_t |= p.prod_sr[b];
       }
-    float4 x[E];
-    auto load_tile = [&](uint64_t tl) {
+    // Two tiles in registers: tile j is split into its stage while tile
+    // j + 1's loads are in flight; then tile j + 2's loads are issued.
+    float4 xa[E], xb[E];
+    auto load_tile = [&](float4(&x)[E], uint64_t tl) {
       const uint64_t tb = tile_base(tl, p) | a_t;
 #pragma unroll
       for (int i = 0; i < E; ++i)
         if (t + i * kTcProdThreads < p.npairs) {
-          const uint64_t a = tb | p.step_addr[i];
+          const uint64_t a = tb | p.prod_step_addr[i];
           if (p.pair_vec) {
             x[i] = *reinterpret_cast<const float4*>(psi + a);
           } else {
@@ -329,16 +340,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
         }
     };
-    uint64_t tile = blockIdx.x;
-    if (tile < p.n_tiles) load_tile(tile);
-    for (uint32_t j = 0; tile < p.n_tiles; ++j, tile += stride) {
+    auto put = [&](const float4(&x)[E], uint32_t j) -> bool {
       const int st = (int)(j & 1u);
-      if (!mbar_wait(empty + st, ((j >> 1) & 1u) ^ 1u, err, p.wait_ns)) break;
+      if (!mbar_wait(empty + st, ((j >> 1) & 1u) ^ 1u, err, p.wait_ns)) return false;
       unsigned char* a_hi = smem + st * S::kStageA;
 #pragma unroll
       for (int i = 0; i < E; ++i)
         if (t + i * kTcProdThreads < p.npairs) {
-          const uint32_t sr = sr_t | p.step_sr[i];
+          const uint32_t sr = sr_t | p.prod_step_sr[i];
           const uint32_t off = sw128_off((int)(sr >> 8), 2 * (int)(sr & 0xFFu), kTcRows);
           const float4 h =
               make_float4(tf32_round(x[i].x), tf32_round(x[i].y), tf32_round(x[i].z), tf32_round(x[i].w));
@@ -349,7 +358,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
       fence_async_smem();
       mbar_arrive(full + st);
-      if (tile + stride < p.n_tiles) load_tile(tile + stride);
+      return true;
+    };
+    uint64_t tile = blockIdx.x;
+    if (tile < p.n_tiles) load_tile(xa, tile);
+    if (tile + stride < p.n_tiles) load_tile(xb, tile + stride);
+    for (uint32_t j = 0; tile < p.n_tiles; j += 2, tile += 2 * stride) {
+      if (!put(xa, j)) break;
+      if (tile + 2 * stride < p.n_tiles) load_tile(xa, tile + 2 * stride);
+      if (tile + stride >= p.n_tiles) break;
+      if (!put(xb, j + 1)) break;
+      if (tile + 3 * stride < p.n_tiles) load_tile(xb, tile + 3 * stride);
     }
     __syncwarp();
   } else if (warp == kTcMmaWarp) {
@@ -400,6 +419,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncwarp();
   } else {
     // ---- epilogue (warps 0-7; warp w reads lanes 32 (w % 4) + lane, column half w / 4) ----
+    constexpr int E = S::kEpiPairs;
     constexpr int kOut4 = S::kStageStride / 2;
     constexpr int kHalf = K / 2;
     float4* out = reinterpret_cast<float4*>(smem + S::kOffOut);  // row r: pairs (s, s + 1)
@@ -675,7 +695,7 @@ qs_status launch_tensor_core(qs_state s, const DenseGeom& g, const double* U) {
   for (int j = 1; j < KQ; ++j) bits.push_back({g.targets[order[j]], 1u << j});
   for (int r = 0; r < rb; ++r) bits.push_back({g.free_pos[r], (1u << r) << 8});
   std::sort(bits.begin(), bits.end());
-  // 8 thread bits, then up to 3 step bits.
+  // Epilogue: 8 thread bits, then up to 3 step bits; producers: 9 and 2.
   for (int b = 0; b < (int)bits.size(); ++b) {
     const uint64_t ab = 1ull << bits[b].first;
     const uint32_t sb = bits[b].second;
@@ -687,6 +707,16 @@ qs_status launch_tensor_core(qs_state s, const DenseGeom& g, const double* U) {
         if ((i >> (b - 8)) & 1) {
           p.step_addr[i] |= ab;
           p.step_sr[i] |= sb;
+        }
+    }
+    if (b < 9) {
+      p.prod_addr[b] = ab;
+      p.prod_sr[b] = sb;
+    } else {
+      for (int i = 0; i < 4; ++i)
+        if ((i >> (b - 9)) & 1) {
+          p.prod_step_addr[i] |= ab;
+          p.prod_step_sr[i] |= sb;
         }
     }
   }
