@@ -28,7 +28,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <vector>
 
 #include "qs_internal.h"
@@ -732,16 +731,12 @@ qs_status launch_tensor_core(qs_state s, const DenseGeom& g, const double* U) {
   uint32_t* err = error_word(s);
   if (!err) return fail(QS_ERR_CUDA, "device error word unavailable");
   using S = TcShape<KQ>;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_dense_tc<KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
-    // All of the unified L1 / shared array as shared memory.
-    if (attr_err == cudaSuccess)
-      attr_err = cudaFuncSetAttribute(k_dense_tc<KQ>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                      (int)cudaSharedmemCarveoutMaxShared);
-  });
-  if (attr_err != cudaSuccess) return cuda_fail(attr_err, "k_dense_tc set-up");
+  // Set on every launch (a host call of microseconds against a launch of
+  // milliseconds), so the state's current device has them too.
+  QS_CUDA(cudaFuncSetAttribute(k_dense_tc<KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem));
+  // All of the unified L1 / shared array as shared memory.
+  QS_CUDA(cudaFuncSetAttribute(k_dense_tc<KQ>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared));
   // One CTA per SM (its pipeline holds up to four tiles).
   const uint64_t cap = (uint64_t)sm_count(s->device);
   const unsigned grid = (unsigned)(p.n_tiles < cap ? p.n_tiles : cap);
