@@ -775,7 +775,25 @@ def measure_dense_k(qs, torch, psi_host, seed=2540):
                     if k == 5 and (best is None or gbs > best[1]["gbs"]):
                         best = (label, v)
                 res["launches"][f"k{k}_{label}_{eng}"] = v
+    # Eight dense 3-target gates over one set of 5 qubits through qs_fuse_run:
+    # composed into one 5-target matrix (one pass) against one pass per gate.
     qs.qs_set_tensor_cores(h, 2)
+    five = [0, 7, 15, 22, n - 1]
+    circ = qs.Circuit([W.gk([five[i] for i in rng.choice(5, size=3, replace=False)], W.haar_unitary(8, rng))
+                       for _ in range(8)])
+    blk = {}
+    for label_b, mf in (("composed", 0), ("gate_by_gate", 1)):
+        qs.qs_fuse_run(h, circ, qs.run_opts(max_fuse=mf))
+        ts = []
+        for _ in range(3):
+            a, b = _events(torch)
+            a.record(stream)
+            qs.qs_fuse_run(h, circ, qs.run_opts(max_fuse=mf))
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        blk[label_b] = {"ms": statistics.median(ts), **qs.qs_last_run_stats(h)}
+    res["dense_block_8_gates_3q_on_5_qubits"] = blk
     label, v = best
     res["roofline_tc_k5"] = {"bound": "hbm", "targets": label, "achieved": v["gbs"], "peak": peak, "unit": "GB/s",
                              "frac": v["gbs"] / peak, "peak_source": peak_src,
@@ -918,7 +936,9 @@ def summarize_extras(ex, peak):
                                  "tc_tensor_frac": r(rf["tensor_frac"], 3),
                                  "cuda_core_gbs": r(max(v["gbs"] for key, v in dk["launches"].items()
                                                         if key.startswith("k5_") and key.endswith("cuda_cores"))),
-                                 "err_over_bound": r(dk["tc_k5_sampled_err_over_fp32_bound"], 3)}
+                                 "err_over_bound": r(dk["tc_k5_sampled_err_over_fp32_bound"], 3),
+                                 "block_8x3q_ms": {k: r(v["ms"], 2) for k, v in
+                                                   dk.get("dense_block_8_gates_3q_on_5_qubits", {}).items()}}
     sp = ex.get("split_32q_c128")
     if sp:
         s["split_32q_gbs"] = {"local": r(sp["local_gate_q20"]["gbs"]), "global": r(sp["global_gate_swap_in"]["gbs"])}

@@ -237,8 +237,11 @@ typedef struct {
   int32_t reserved[6];
 } qs_run_opts;
 
-/* Run a circuit on one state.  Consecutive gates on the same one or two
- * qubits are first multiplied into one 2x2 / 4x4 matrix in FP64 where that
+/* Run a circuit on one state.  A dense gate on 3..5 targets is first
+ * multiplied in FP64 with the gates after it that stay within 5 qubits (gates
+ * on other qubits are stepped over where they commute with the block) into
+ * one matrix applied in one pass.  Consecutive gates on the same one or two
+ * qubits are multiplied into one 2x2 / 4x4 matrix in FP64 where that
  * saves arithmetic (never for permutations); then gates whose qubits fit
  * one block of at most max_fuse qubits are applied by one fused kernel that
  * keeps the block's amplitudes on chip for all of its gates (related work,
@@ -258,7 +261,11 @@ qs_status qs_fuse_run(qs_state s, const qs_circuit* c, const qs_run_opts* opts);
 typedef struct {
   int64_t fused_launches;  /* fused-block kernels (one HBM pass each) */
   int64_t gate_launches;   /* gates run on the per-gate kernels */
-  int64_t reserved[6];
+  int64_t dense_blocks;    /* dense gates on 3..5 targets composed with the
+                              gates after them on at most 5 qubits into one
+                              matrix (one per-gate launch each) */
+  int64_t dense_gates;     /* gates those blocks absorbed */
+  int64_t reserved[4];
 } qs_run_stats;
 qs_status qs_last_run_stats(qs_state s, qs_run_stats* out);
 

@@ -134,6 +134,8 @@ qs_status qs_fuse_run(qs_state s, const qs_circuit* c, const qs_run_opts* opts) 
   }
   s->run_fused_launches = 0;
   s->run_gate_launches = 0;
+  s->run_dense_blocks = 0;
+  s->run_dense_gates = 0;
   if (c->n_gates == 0) return QS_OK;
   if (s->split) return split_run(s, c, max_fuse);
   if (max_fuse != 1) return run_fused(s, c, max_fuse == 0 ? tuned_max_fuse(s) : max_fuse);
@@ -147,6 +149,8 @@ qs_status qs_last_run_stats(qs_state s, qs_run_stats* out) {
   std::memset(out, 0, sizeof(*out));
   out->fused_launches = s->run_fused_launches;
   out->gate_launches = s->run_gate_launches;
+  out->dense_blocks = s->run_dense_blocks;
+  out->dense_gates = s->run_dense_gates;
   return QS_OK;
 }
 

@@ -30,6 +30,8 @@ struct qs_state_s {
   // Launches of the last qs_fuse_run on this state (qs_last_run_stats).
   int64_t run_fused_launches = 0;
   int64_t run_gate_launches = 0;
+  int64_t run_dense_blocks = 0;  // composed dense blocks (qs_densefuse.h)
+  int64_t run_dense_gates = 0;   // gates they absorbed
   // Split state (qs_create_split): segments, placement and qubit map
   // (qs_split.cu); nullptr for a state in one allocation.
   void* split = nullptr;

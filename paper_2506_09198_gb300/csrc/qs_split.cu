@@ -265,9 +265,13 @@ qs_status flush_run(qs_state s, std::vector<SegCirc>& pend, int max_fuse) {
     } else {
       seg->run_fused_launches = 0;
       seg->run_gate_launches = 0;
+      seg->run_dense_blocks = 0;
+      seg->run_dense_gates = 0;
       st = run_fused(seg, &c, max_fuse == 0 ? fuse_width_for(seg) : max_fuse);
       fused += seg->run_fused_launches;
       single += seg->run_gate_launches;
+      s->run_dense_blocks += seg->run_dense_blocks;
+      s->run_dense_gates += seg->run_dense_gates;
     }
     if (st != QS_OK) return st;
     pend[a].clear();
@@ -289,6 +293,8 @@ qs_status split_run(qs_state s, const qs_circuit* c, int max_fuse) {
   std::vector<SegCirc> pend(nseg);
   s->run_fused_launches = 0;
   s->run_gate_launches = 0;
+  s->run_dense_blocks = 0;
+  s->run_dense_gates = 0;
   for (int64_t gi = 0; gi < c->n_gates; ++gi) {
     const qs_gate& g = c->gates[gi];
     const int k = g.k;

@@ -31,6 +31,7 @@
 #include "qs_tile.cuh"
 #include "qs_tile_dev.cuh"
 #include "qs_fuser.h"
+#include "qs_densefuse.h"
 #include "qs_matfuse.h"
 
 namespace qs {
@@ -380,6 +381,12 @@ qs_status run_fused(qs_state s, const qs_circuit* c, int max_high) {
   for (int64_t i = 0; i < c->n_gates; ++i) gates.push_back(normalise(c, c->gates[i]));
   XPusher xp;   // owns conjugated tables until the blocks are launched
   gates = xp.run(gates);
+  // Dense blocks first, on the circuit's own order (the 1q/2q fusion below
+  // moves pending small gates next to the gates that close them).
+  DenseFuser df;  // owns the composed dense blocks until they are launched
+  gates = df.run(gates);
+  s->run_dense_blocks += df.blocks();
+  s->run_dense_gates += df.absorbed();
   MatFuser mf;  // owns the fused matrices until the blocks are launched
   gates = mf.run(gates);
   if (max_high > kTileMaxHigh) max_high = kTileMaxHigh;

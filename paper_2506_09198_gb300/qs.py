@@ -45,7 +45,8 @@ class qs_circuit(ctypes.Structure):
 
 class qs_run_stats(ctypes.Structure):
     _fields_ = [("fused_launches", ctypes.c_int64), ("gate_launches", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 6)]
+                ("dense_blocks", ctypes.c_int64), ("dense_gates", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 4)]
 
 
 class qs_run_opts(ctypes.Structure):
@@ -386,7 +387,8 @@ def qs_last_run_stats(h) -> dict:
     """Launch counts of the last qs_fuse_run on h."""
     st = qs_run_stats()
     _check(_lib.qs_last_run_stats(h, ctypes.byref(st)))
-    return {"fused_launches": st.fused_launches, "gate_launches": st.gate_launches}
+    return {"fused_launches": st.fused_launches, "gate_launches": st.gate_launches,
+            "dense_blocks": st.dense_blocks, "dense_gates": st.dense_gates}
 
 
 def qs_autotune(h, circuit: Circuit):

@@ -278,3 +278,44 @@ def test_dense_tc_wait_runs_out_and_context_survives(restore_wait_limit):
     got = st.read()
     st.close()
     check(got, stored_input(psi, "c64_tc"), [W.gk(tg, U)], "c64_tc", "after a timeout")
+
+
+@pytest.mark.parametrize("mode", ["c64_tc", "c64_cc", "c128_df"])
+def test_dense_blocks_composed_in_fused_runs(mode):
+    """qs_fuse_run composes a dense gate on 3..5 targets with the gates after
+    it that stay within 5 qubits (one pass instead of one per dense gate):
+    gates on other qubits are stepped over and close their qubits to the
+    block, so a gate after a stepped-over gate on a shared qubit is not moved
+    ahead of it.  The result matches the oracle, and the three dense gates
+    form one composed block."""
+    q = qs()
+    n = 14
+    rng = W.rng_for(7800)
+    gates = [W.g1(t, W.mat_h()) for t in range(n)]
+    gates += [W.gk([2, 5, 9], W.haar_unitary(8, rng)),                  # starts a block on {2, 5, 9}
+              W.g1(0, W.haar_unitary(2, rng)),                          # disjoint: stepped over
+              W.g1(5, W.haar_unitary(2, rng)),                          # inside: absorbed
+              W.CNOT(2, 11),                                            # widens to {2, 5, 9, 11}
+              W.gk([9, 11, 5], W.haar_unitary(8, rng), ctrls=(2,)),     # inside
+              W.CNOT(0, 1),                                             # disjoint
+              W.gk([2, 5, 9, 11, 12], W.haar_unitary(32, rng)),         # widens to 5 qubits
+              W.CZ(12, 13),                                             # 13 outside: stepped over, closes 12, 13
+              W.g1(12, W.mat_h()),                                      # on a closed qubit: stays after the CZ
+              W.g1(9, W.haar_unitary(2, rng)),                          # inside, open: absorbed
+              W.g1(13, W.haar_unitary(2, rng))]
+    psi = W.random_state(n, rng)
+    x_in = stored_input(psi, mode)
+    st = make_state(n, mode, psi)
+    st.run(gates)
+    stats = q.qs_last_run_stats(st.h)
+    got = st.read()
+    st.close()
+    ref = O.run_circuit(x_in.copy(), gates)
+    if mode.startswith("c128"):
+        assert float(np.max(np.abs(got - ref))) <= C128_TOL
+    else:
+        f = abs(np.vdot(got, ref)) ** 2 / (np.vdot(got, got).real * np.vdot(ref, ref).real)
+        assert f >= 1 - 1e-6 and float(np.max(np.abs(got - ref))) <= 2e-6
+    # One block: the three dense gates, g1(5), CNOT(2, 11) and the trailing
+    # g1(9).
+    assert stats["dense_blocks"] == 1 and stats["dense_gates"] == 6, stats
