@@ -352,8 +352,9 @@ qs_status qs_probs_noalloc(const void* device_state, int n, qs_dtype dtype, cons
 
 /* Limit of every bounded wait inside the fused and batched kernels (a wait
  * on a tile copy or on the warps that consume it), in seconds, 0 to 60;
- * default 2.  Applies to launches queued after the call, process-wide.  A
- * wait that runs out stops the kernel early: the kernel records
+ * default 2.  Applies to launches queued after the call, process-wide; with
+ * 0 a wait gives up at once if its barrier is not complete when it first
+ * checks.  A wait that runs out stops the kernel early: the kernel records
  * QS_ERR_TIMEOUT in the state's error word, lets its own copies land and
  * returns, so the context stays usable and the state's contents are
  * unspecified.  Production code keeps the default; a short limit is for

@@ -1,8 +1,9 @@
 // Fused-block kernel and host fuser.
 //
-// k_tile is persistent (one or two CTAs per SM).  A producer warp streams
-// tiles between HBM and shared memory with bulk asynchronous copies
-// (cp.async.bulk, the TMA engine) — one copy per contiguous chunk, completion
+// k_tile is persistent (one or two CTAs per SM).  A producer (a warp of its
+// own, or consumer thread 0 between its tiles for float-float blocks with
+// 4x4 ops) streams tiles between HBM and shared memory with bulk asynchronous
+// copies (cp.async.bulk, the TMA engine) — one copy per contiguous chunk, completion
 // tracked by mbarrier transaction counts — through a ring of kStages buffers.
 // Eight consumer warps apply the block's gates to the tile in shared memory,
 // one gate after another, and hand the buffer back; the producer writes it to
@@ -37,7 +38,7 @@
 namespace qs {
 
 template <class TP>
-__global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_tile(typename TP::Glob* __restrict__ psi,
+__global__ void __launch_bounds__(tile_threads<TP>(), kTileMinCtas) k_tile(typename TP::Glob* __restrict__ psi,
                                                        const __grid_constant__ TilePlan<typename TP::M::Coef> plan,
                                                        uint32_t* __restrict__ err) {
   using Glob = typename TP::Glob;
@@ -79,6 +80,73 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinCtas) k_tile(typename TP
     }
   }
   __syncthreads();
+
+  if constexpr (TP::kFoldProducer) {
+    // ------------- consumers; thread 0 also moves the tiles -------------
+    // This CTA's tiles are tau = blockIdx.x + j * gridDim.x, j < n_mine.
+    // Tiles j + 1 .. j + kAhead are in flight while tile j is consumed;
+    // after tile j, thread 0 waits until every consumer is done with it,
+    // stores it, and loads tile j + kAhead into the stage that tile j - 1
+    // left (whose store has read it by then: at most one store group, tile
+    // j's, may still be reading).  Warp 0's other lanes wait at __syncwarp.
+    constexpr uint32_t kAhead = kStages - 1;
+    const uint32_t n_mine =
+        plan.n_tiles > blockIdx.x ? (uint32_t)((plan.n_tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0u;
+    auto tile_at = [&](uint32_t j) {
+      return tile_base(blockIdx.x + (uint64_t)j * gridDim.x, plan.L, plan.m, plan.base_high);
+    };
+    auto issue_load = [&](uint32_t j) {
+      const int s = (int)(j % kStages);
+      unsigned char* buf = smem + (size_t)s * tile_bytes;
+      const uint64_t b = tile_at(j);
+      mbar_expect_tx(&full[s], tile_bytes);
+      for (uint32_t c = 0; c < n_chunks; ++c)
+        bulk_load(buf + (size_t)c * chunk_bytes, psi + b + plan.chunk_off[c], chunk_bytes, &full[s]);
+    };
+    uint32_t loads_issued = 0;
+    if (tid == 0)
+      for (; loads_issued < n_mine && loads_issued < kAhead; ++loads_issued) issue_load(loads_issued);
+    bool stop = false;  // thread 0: a wait of the copying role gave up
+    uint32_t j = 0;
+    for (; j < n_mine; ++j) {
+      const int s = (int)(j % kStages);
+      const bool ok = mbar_wait(&full[s], (j / kStages) & 1u, err, plan.wait_ns);
+      if (consumers_any(!ok || stop)) break;
+      Sm* t = reinterpret_cast<Sm*>(smem + (size_t)s * tile_bytes);
+      consume_tile<TP>(reinterpret_cast<unsigned char*>(t), s_ops, plan.nops, s_coefs, plan.perm, plan.fmt,
+                       static_cast<const typename TP::Phase*>(plan.phase_tab), plan.L + plan.m, tile_at(j), tid);
+      fence_async_smem();
+      mbar_arrive(&done[s]);
+      if (tid == 0) {
+        if (!mbar_wait(&done[s], (j / kStages) & 1u, err, plan.wait_ns)) {
+          stop = true;
+        } else {
+          const uint64_t b = tile_at(j);
+          unsigned char* buf = smem + (size_t)s * tile_bytes;
+          for (uint32_t c = 0; c < n_chunks; ++c)
+            bulk_store(psi + b + plan.chunk_off[c], buf + (size_t)c * chunk_bytes, chunk_bytes);
+          bulk_commit();
+          if (loads_issued < n_mine) {
+            bulk_wait_read_one();
+            issue_load(loads_issued++);
+          }
+        }
+      }
+      __syncwarp();
+    }
+    if (tid == 0) {
+      // After an early stop, let the loads still in flight land (bounded;
+      // they are plain in-range reads) before shared memory goes away.
+      for (uint32_t jj = j; jj < loads_issued; ++jj) {
+        const int s = (int)(jj % kStages);
+        const uint64_t t0 = global_ns();
+        while (!mbar_try(&full[s], (jj / kStages) & 1u) && global_ns() - t0 < kDrainNs) {
+        }
+      }
+      bulk_wait_all();
+    }
+    return;
+  }
 
   if (tid >= kTileConsumers) {
     // ---------------- producer ----------------
@@ -199,7 +267,7 @@ void fill_plan(TilePlan<Coef>* plan, int n, const BlockOut<Coef>& bo) {
 }
 
 template <class TP>
-qs_status launch_plan(qs_state s, const TilePlan<typename TP::M::Coef>& plan) {
+qs_status launch_plan_as(qs_state s, const TilePlan<typename TP::M::Coef>& plan) {
   using Coef = typename TP::M::Coef;
   const size_t tile_bytes = sizeof(typename TP::Glob) << (plan.L + plan.m);
   const size_t smem = kStages * tile_bytes + 2 * kStages * sizeof(uint64_t) +
@@ -223,7 +291,7 @@ qs_status launch_plan(qs_state s, const TilePlan<typename TP::M::Coef>& plan) {
     const int key = (int)smem;
     auto it = occ_cache.find(key);
     if (it == occ_cache.end()) {
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTileThreads, smem) != cudaSuccess || occ < 1)
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, tile_threads<TP>(), smem) != cudaSuccess || occ < 1)
         occ = 1;
       occ_cache[key] = occ;
     } else {
@@ -234,13 +302,24 @@ qs_status launch_plan(qs_state s, const TilePlan<typename TP::M::Coef>& plan) {
   const unsigned grid = (unsigned)(plan.n_tiles < full ? plan.n_tiles : full);
   uint32_t* err = error_word(s);
   if (!err) return fail(QS_ERR_CUDA, "device error word unavailable");
-  kern<<<grid, kTileThreads, smem, s->stream>>>((typename TP::Glob*)s->psi, plan, err);
+  kern<<<grid, tile_threads<TP>(), smem, s->stream>>>((typename TP::Glob*)s->psi, plan, err);
   ++s->run_fused_launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess)
     return fail(QS_ERR_CUDA, "k_tile launch (grid %u, smem %zu, plan %zu bytes, %d ops, L %d, m %d): %s", grid, smem,
                 sizeof(plan), plan.nops, plan.L, plan.m, cudaGetErrorString(e));
   return QS_OK;
+}
+
+// Float-float blocks with 4x4 ops run with warp 0 as the producer (no
+// spills in the 4x4 rows); the others keep the producer warp.
+template <class TP>
+qs_status launch_plan(qs_state s, const TilePlan<typename TP::M::Coef>& plan) {
+  if constexpr (std::is_same<TP, TileDF>::value) {
+    for (int i = 0; i < plan.nops; ++i)
+      if (plan.ops[i].kind == TOP_DENSE2) return launch_plan_as<TileDFFold>(s, plan);
+  }
+  return launch_plan_as<TP>(s, plan);
 }
 
 qs_status dispatch_single(qs_state s, const FGate& g) {

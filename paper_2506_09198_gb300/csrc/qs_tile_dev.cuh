@@ -26,6 +26,12 @@ namespace qs {
 constexpr int kTileConsumersLog = QS_TILE_CONSUMERS_LOG;
 constexpr int kTileConsumers = 1 << kTileConsumersLog;
 constexpr int kTileThreads = kTileConsumers + 32;
+// Threads of a CTA under policy TP: the consumers, plus a producer warp
+// unless consumer thread 0 takes that role (TP::kFoldProducer).
+template <class TP>
+constexpr int tile_threads() {
+  return TP::kFoldProducer ? kTileConsumers : kTileThreads;
+}
 constexpr int kStages = QS_TILE_STAGES;
 constexpr int kTileMinCtas = QS_TILE_MIN_CTAS;
 // Bound of the waits that let a CTA's own copies land before it exits after
@@ -61,9 +67,26 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+// Non-blocking check of a phase (try_wait may suspend the thread for a
+// while before it reports an incomplete phase; test_wait does not).
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait (limit_ns of %globaltimer): false when it gave up (timeout
-// recorded, or another thread already recorded an error).
+// recorded, or another thread already recorded an error).  A limit of 0
+// gives up at once if the phase is not complete when first checked.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* err, uint64_t limit_ns) {
+  if (limit_ns == 0) {
+    if (mbar_test(bar, parity)) return true;
+    atomicCAS(err, 0u, 1u);
+    return false;
+  }
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (!mbar_try(bar, parity)) {
@@ -88,6 +111,9 @@ __device__ __forceinline__ void bulk_store(void* dst, const void* src_smem, uint
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// At most one committed bulk group of this thread may still be reading
+// shared memory.
+__device__ __forceinline__ void bulk_wait_read_one() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void consumers_sync() {
@@ -109,6 +135,8 @@ __device__ __forceinline__ bool consumers_any(bool v) {
 // ---------------------------------------------------------------------------
 struct TileF32 {
   using M = MathF32;
+  // A producer warp of its own beside the eight consumer warps.
+  static constexpr bool kFoldProducer = false;
   // Copy a 2x2 op's four coefficients to registers before the pairs.
   static constexpr bool kHoistCoefs = true;
   // Uncontrolled 4x4 ops take the quads two at a time (one coefficient load
@@ -191,6 +219,7 @@ __device__ __forceinline__ double dneg(double x) {
 
 struct TileF64 {
   using M = MathF64;
+  static constexpr bool kFoldProducer = false;
   static constexpr bool kHoistCoefs = true;
   static constexpr bool kQuadPairs = false;
   // Stage the block's ops and coefficients in shared memory.
@@ -236,6 +265,7 @@ struct TileF64 {
 // Float-float tile element: (re_h, im_h, re_l, im_l), |l| <= ulp(h)/2.
 struct TileDF {
   using M = MathDF;
+  static constexpr bool kFoldProducer = false;
   static constexpr bool kQuadPairs = false;
   // Plans are staged in shared memory: the lanes of a diagonal op gather
   // different coefficients, which the parameter bank would serialise.
@@ -320,6 +350,16 @@ struct TileDF {
   static __device__ __forceinline__ Sm neg_if(Sm a, uint32_t s) {
     return make_float4(fxor(a.x, s), fxor(a.y, s), fxor(a.z, s), fxor(a.w, s));
   }
+};
+
+// TileDF with consumer thread 0 issuing the copies between its tiles: two CTAs
+// of eight warps (16 per SM, four on each register partition) leave 128
+// registers a thread, where a ninth producer warp per CTA (five warps on
+// some partitions) caps them at 96 and makes the float-float 4x4 ops spill.
+// Thread 0 then waits for the slowest warp once per tile, which costs more
+// than it saves on blocks without 4x4 ops.
+struct TileDFFold : TileDF {
+  static constexpr bool kFoldProducer = true;
 };
 
 // The batched kernel stages float-float plans like k_tile does.
