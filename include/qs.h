@@ -271,8 +271,11 @@ qs_status qs_last_run_stats(qs_state s, qs_run_stats* out);
 
 /* Autotuner for fusion: run circuit c on s with every fusion setting
  * (max_fuse 1..6, which also sets the tile shape: 2^max_fuse strided chunks
- * of contiguous amplitudes), time each on the device, and remember the
- * fastest fused setting for states of s's dtype, math mode and qubit count;
+ * of contiguous amplitudes), time each on the device (the fastest of three
+ * runs after an untimed one), and remember the fastest fused setting for
+ * states of s's dtype, math mode and qubit count, whatever circuit later
+ * runs on them (tune on the circuit that matters; a width tuned on one
+ * circuit family is a guess for another);
  * qs_fuse_run with max_fuse = 0 then uses it (default 4 before any tuning).
  * s is scratch: it is reset to |0...0> before each trial and holds the last
  * trial's result afterwards.  Synchronous.  best_max_fuse and best_ms may be

@@ -168,22 +168,27 @@ qs_status qs_autotune(qs_state s, const qs_circuit* c, int* best_max_fuse, doubl
   int best = 1;
   float best_t = 0.f;
   qs_status st = QS_OK;
+  constexpr int kTimedReps = 3;
   for (int mf = 1; mf <= 6 && st == QS_OK; ++mf) {
-    // one untimed run (kernel loading), one timed
-    for (int rep = 0; rep < 2 && st == QS_OK; ++rep) {
+    // one untimed run (kernel loading), then the fastest of kTimedReps
+    float ms = 0.f;
+    for (int rep = 0; rep <= kTimedReps && st == QS_OK; ++rep) {
       st = launch_init_basis(s, 0);
       if (st != QS_OK) break;
-      if (rep == 1 && cudaEventRecord(a, s->stream) != cudaSuccess) st = fail(QS_ERR_CUDA, "event record");
+      if (rep > 0 && cudaEventRecord(a, s->stream) != cudaSuccess) st = fail(QS_ERR_CUDA, "event record");
       if (st == QS_OK) st = mf == 1 ? qs_fuse_run_gatewise(s, c) : run_fused(s, c, mf);
-      if (st == QS_OK && rep == 1 && cudaEventRecord(b, s->stream) != cudaSuccess) st = fail(QS_ERR_CUDA, "event record");
+      if (st != QS_OK || rep == 0) continue;
+      if (cudaEventRecord(b, s->stream) != cudaSuccess) {
+        st = fail(QS_ERR_CUDA, "event record");
+      } else if (cudaEventSynchronize(b) != cudaSuccess) {
+        st = fail(QS_ERR_CUDA, "event synchronize");
+      } else {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, a, b);
+        if (rep == 1 || t < ms) ms = t;
+      }
     }
     if (st != QS_OK) break;
-    if (cudaEventSynchronize(b) != cudaSuccess) {
-      st = fail(QS_ERR_CUDA, "event synchronize");
-      break;
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
     if (mf == 1 || ms < best_t) {
       best = mf;
       best_t = ms;
