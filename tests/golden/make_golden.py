@@ -2,12 +2,12 @@
 oracle (``oracle/``); nothing here comes from the CUDA library.
 
 access_6q.txt: which amplitude indices a single-qubit gate mixes on a
-6-qubit state, for each target 0..5 (the access pattern of Fig. 2), and
-which of those pairs a gate controlled by qubit 2 updates (Fig. 3).  The
+6-qubit state, for each target 0..5 (the access pattern of Fig. 3), and
+which of those pairs a gate controlled by qubit 2 updates (Fig. 4).  The
 pairs are found by applying the oracle's Hadamard to every basis state: a
 basis state |i> with bit t clear spreads over exactly {i, partner}.  They are
 listed in ascending order of the lower index, which is the task order of the
-paper's Hadamard kernel (Sec. III-B).
+paper's Hadamard kernel (Algorithm 1, Sec. II-B).
 
 Run from the repository root: python tests/golden/make_golden.py
 """
@@ -51,9 +51,9 @@ def controlled_updates(t):
 
 def render() -> str:
     lines = [
-        "# Amplitude index pairs mixed by a single-qubit gate on a 6-qubit state (Fig. 2),",
-        "# lower index ascending = task order of the Hadamard kernel (Sec. III-B), and the pairs",
-        f"# a gate controlled by qubit {CONTROL} updates (Fig. 3).  Written by make_golden.py from the oracle.",
+        "# Amplitude index pairs mixed by a single-qubit gate on a 6-qubit state (Fig. 3),",
+        "# lower index ascending = task order of the Hadamard kernel (Algorithm 1), and the pairs",
+        f"# a gate controlled by qubit {CONTROL} updates (Fig. 4).  Written by make_golden.py from the oracle.",
     ]
     for t in range(N):
         lines.append(f"pairs t={t}: " + " ".join(f"{a}-{b}" for a, b in pairs(t)))

@@ -1,12 +1,12 @@
 """The oracle's single-qubit access pattern against the paper (CPU only).
 
 tests/golden/access_6q.txt lists, for a 6-qubit state, the amplitude pairs
-that a single-qubit gate on each target mixes (the pattern Fig. 2 draws for
+that a single-qubit gate on each target mixes (the pattern Fig. 3 draws for
 targets 0..5) and the pairs that a gate controlled by qubit 2 updates
-(Fig. 3: only pairs whose control bit is 1).  The file is written by
+(Fig. 4: only pairs whose control bit is 1).  The file is written by
 tests/golden/make_golden.py from the oracle.  Here it is checked three ways:
 the oracle still produces it; its pairs, in order, are those of the paper's
-Hadamard kernel (Sec. III-B), where task k of target t works on the lower
+Hadamard kernel (Algorithm 1, Sec. II-B), where task k of target t works on the lower
 index made of k's bits above t shifted up by one place and k's bits below t,
 and on that index plus 2^t; and the controlled pairs are exactly those whose
 lower index has bit 2 set.
