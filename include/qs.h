@@ -176,7 +176,8 @@ qs_status qs_apply_ctrl(qs_state s, const int* ctrls, int nctrl, int target, con
  * targets (1 <= k <= QS_MAX_DENSE) where all nctrl controls are 1.  Sub-
  * register value s = sum_j bit(i, targets[j]) 2^j indexes rows and columns;
  * each group of 2^k amplitudes sharing the other bits is multiplied by U
- * (Sec. II-B: a k-qubit gate is a 2^k x 2^k unitary on its index bits).
+ * (the in-place matrix-vector product of Sec. II-C and Fig. 3, extended
+ * from the paper's one and two targets to k).
  * Diagonal and permutation matrices run as qs_apply_diag / qs_apply_perm;
  * dense matrices on 3..5 targets run on the tensor cores or the FP32 CUDA
  * cores for complex64 states (qs_set_tensor_cores), on the CUDA cores in the

@@ -1,7 +1,9 @@
 // Dense gates on 3..5 targets: every group of d = 2^k amplitudes that share
 // their non-target bits (and have all controls 1) is multiplied by the
-// 2^k x 2^k matrix U (Sec. II-B: a k-qubit gate acts as a 2^k x 2^k
-// unitary on the index bits it targets; Algorithm 1 is the k = 1 case).
+// 2^k x 2^k matrix U.  The paper applies a gate as an in-place
+// matrix-vector multiplication (Sec. II-C, Fig. 3) with kernels for one and
+// two targets (Algorithm 1 is the one-target case); a gate on k targets is
+// the same product with the 2^k x 2^k matrix on the index bits it targets.
 //
 // Two kernels:
 //
