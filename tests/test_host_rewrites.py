@@ -11,6 +11,12 @@ tests run the rewrites on the CPU through a small harness
 apply both the original and the rewritten list to the same seeded state with
 the oracle, and require the two states to agree within 1e-12, the
 complex128 bar.  They also check that each rewrite fired.
+
+The blocks that follow move gates ahead of gates they commute with (disjoint
+qubits; diagonal gates need no tile qubits).  test_block_order applies the
+rewritten gates in the order the fused runner executes them, block by block,
+for both tile policies and several fusion widths, and compares with the
+circuit's own order.
 """
 import ctypes
 import os
@@ -55,6 +61,9 @@ def harness(oracle_mod):
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     h = ctypes.CDLL(out)
+    h.rw_block_order.restype = ctypes.c_int64
+    h.rw_block_order.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), ctypes.c_int64]
     h.rw_rewrite.restype = ctypes.c_int64
     h.rw_rewrite.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(RwGate), ctypes.c_int64,
                              ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.POINTER(ctypes.c_uint32),
@@ -198,3 +207,43 @@ def test_workload_circuits(oracle_mod, harness, name):
     else:
         gates = W.shor_like(n, seed=9301)[0]
     check(oracle_mod, harness, n, gates, X_PUSH | DENSE | MATFUSE, 9302)
+
+
+@pytest.mark.parametrize("dtype_name", ["c128", "c64"])
+@pytest.mark.parametrize("max_high", [2, 4, 6])
+@pytest.mark.parametrize("name", ["varied", "qft", "rqc", "grover", "shor"])
+def test_block_order(oracle_mod, harness, dtype_name, max_high, name):
+    from paper_2506_09198_gb300 import qs
+
+    O = oracle_mod
+    n = 14
+    if name == "varied":
+        gates = varied_circuit(n, 220, 9400 + max_high)
+    elif name == "qft":
+        gates = W.qft(list(range(n)))
+    elif name == "rqc":
+        gates = W.rqc(n, 10, seed=9401)
+    elif name == "grover":
+        gates = W.grover(n, 4321, 3)
+    else:
+        gates = W.shor_like(n, seed=9402)[0]
+    rw = rewrite(harness, gates, X_PUSH | DENSE | MATFUSE)
+    c = qs.Circuit(gates)
+    cap = len(rw) + 8
+    order = np.zeros(cap, dtype=np.int64)
+    block = np.zeros(cap, dtype=np.int32)
+    dt = qs.QS_C128 if dtype_name == "c128" else qs.QS_C64
+    cnt = harness.rw_block_order(ctypes.cast(c.ptr, ctypes.c_void_p), n, dt, max_high,
+                                 order.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                 block.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), cap)
+    assert cnt == len(rw)
+    order, block = order[:cnt], block[:cnt]
+    assert sorted(order.tolist()) == list(range(cnt))  # every gate exactly once
+    assert np.all(np.diff(block) >= 0)
+    psi0 = W.random_state(n, W.rng_for(9403))
+    want = O.run_circuit(psi0.copy(), gates)
+    got = apply_rewritten(O, psi0.copy(), [rw[i] for i in order])
+    err = float(np.max(np.abs(got - want)))
+    assert err <= 1e-12, f"max |diff| {err:.3e}"
+    if name in ("varied", "qft", "rqc"):
+        assert block[-1] + 1 < cnt  # blocks of several gates formed
