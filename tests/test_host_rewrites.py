@@ -54,12 +54,14 @@ def harness(oracle_mod):
     libdir = os.path.dirname(lib)
     os.makedirs(OUT_DIR, exist_ok=True)
     out = os.path.join(OUT_DIR, "librewrite.so")
+    tmp = f"{out}.{os.getpid()}.tmp"  # concurrent test processes each build, then rename
     cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O1", "-std=c++17", "-Xcompiler", "-fPIC",
            "--expt-relaxed-constexpr", "-shared", "-I", os.path.join(ROOT, "include"),
-           "-I", os.path.join(ROOT, "paper_2506_09198_gb300", "csrc"), HARNESS, "-o", out,
+           "-I", os.path.join(ROOT, "paper_2506_09198_gb300", "csrc"), HARNESS, "-o", tmp,
            "-L", libdir, "-lqs", "-Xlinker", "-rpath=" + libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+    os.replace(tmp, out)
     h = ctypes.CDLL(out)
     h.rw_block_order.restype = ctypes.c_int64
     h.rw_block_order.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
